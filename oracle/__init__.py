@@ -1,0 +1,162 @@
+"""CPU oracle for the kNN + covariance step (Sec. III-C1, Eq. 18-20).
+
+TEST INFRASTRUCTURE ONLY: the test-suite, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` are the only callers.  The product package
+never imports this module and shares no code with it.
+
+Functions follow the plain definitions:
+
+* ``knn_brute(q, p, k)``   -- every target's binary32 d2 in the pinned order
+  ``fmaf(dz,dz,fmaf(dy,dy,dx*dx))``, first k under (d2, index) ascending.
+* ``KDTree(p).knn(q, k)``  -- the same answer through a median-split k-d tree
+  (pruning by a proven lower bound of the binary32 d2; ties still visited).
+* ``cov(p, idx, eps)``     -- binary64 neighbourhood covariance with 1/k, and
+  for eps >= 0 the plane regularisation C' = I - (1-eps) n n^T with n the
+  smallest-eigenvalue eigenvector (cyclic Jacobi).
+* ``eig_sym3(c6)``         -- the Jacobi eigen-solver on its own.
+
+Parity of the covariance against the paper's own numbers is unpinned: the
+paper prints no worked example.  The pins live in ``tests/test_oracle_pins.py``
+(closed forms, invariants, exact rational arithmetic, library cross-checks).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_LIB_PATH = os.path.join(_HERE, "liboracle.so")
+_lib = None
+
+CFLAGS = ["-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared", "-pthread"]
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c into liboracle.so next to it (plain gcc, no CUDA)."""
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+        tmp = _LIB_PATH + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", *CFLAGS, "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        lib = ctypes.CDLL(build())
+        i64, i32, f64 = ctypes.c_int64, ctypes.c_int, ctypes.c_double
+        vp = ctypes.c_void_p
+        lib.oracle_knn_brute.argtypes = [vp, i64, vp, i64, i32, vp, vp, i32]
+        lib.oracle_knn_brute.restype = i32
+        lib.oracle_kdtree_build.argtypes = [vp, i64]
+        lib.oracle_kdtree_build.restype = vp
+        lib.oracle_kdtree_free.argtypes = [vp]
+        lib.oracle_kdtree_free.restype = None
+        lib.oracle_kdtree_knn.argtypes = [vp, vp, i64, i32, vp, vp, i32]
+        lib.oracle_kdtree_knn.restype = i32
+        lib.oracle_cov.argtypes = [vp, i64, vp, i64, i32, f64, vp, i32]
+        lib.oracle_cov.restype = i32
+        lib.oracle_eig_sym3.argtypes = [vp, vp, vp]
+        lib.oracle_eig_sym3.restype = None
+        lib.oracle_default_threads.argtypes = []
+        lib.oracle_default_threads.restype = i32
+        _lib = lib
+    return _lib
+
+
+def default_threads() -> int:
+    return int(_load().oracle_default_threads())
+
+
+def _f32x3(a) -> np.ndarray:
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    if a.ndim != 2 or a.shape[1] != 3:
+        raise ValueError("points must be [n,3] float32")
+    return a
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def knn_brute(q, p, k: int, threads: int = 0):
+    """Exact kNN by definition: returns (idx int32 [n,k], d2 float32 [n,k])."""
+    q, p = _f32x3(q), _f32x3(p)
+    n, m = q.shape[0], p.shape[0]
+    idx = np.empty((n, k), np.int32)
+    d2 = np.empty((n, k), np.float32)
+    rc = _load().oracle_knn_brute(_ptr(q), n, _ptr(p), m, int(k), _ptr(idx), _ptr(d2), int(threads))
+    if rc != 0:
+        raise ValueError(f"oracle_knn_brute: bad arguments (k={k}, m={m})")
+    return idx, d2
+
+
+class KDTree:
+    """Median-split k-d tree over p; answers equal knn_brute bit for bit."""
+
+    def __init__(self, p):
+        self._p = _f32x3(p)  # the tree keeps a pointer into this array
+        self.m = self._p.shape[0]
+        self._h = _load().oracle_kdtree_build(_ptr(self._p), self.m)
+        if not self._h:
+            raise ValueError("empty target")
+
+    def knn(self, q, k: int, threads: int = 0):
+        q = _f32x3(q)
+        n = q.shape[0]
+        idx = np.empty((n, k), np.int32)
+        d2 = np.empty((n, k), np.float32)
+        rc = _load().oracle_kdtree_knn(self._h, _ptr(q), n, int(k), _ptr(idx), _ptr(d2), int(threads))
+        if rc != 0:
+            raise ValueError(f"oracle_kdtree_knn: bad arguments (k={k}, m={self.m})")
+        return idx, d2
+
+    def close(self):
+        if self._h:
+            _load().oracle_kdtree_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def cov(p, idx, eps: float, threads: int = 0) -> np.ndarray:
+    """binary64 covariance (eps < 0) or regularised covariance (eps >= 0) of
+    each neighbourhood row of idx over the target p: float64 [n,6] packed
+    (xx, xy, xz, yy, yz, zz)."""
+    p = _f32x3(p)
+    idx = np.ascontiguousarray(idx, dtype=np.int32)
+    if idx.ndim != 2:
+        raise ValueError("idx must be [n,k]")
+    n, k = idx.shape
+    out = np.empty((n, 6), np.float64)
+    rc = _load().oracle_cov(_ptr(p), p.shape[0], _ptr(idx), n, k, float(eps), _ptr(out), int(threads))
+    if rc != 0:
+        raise ValueError(f"oracle_cov: bad arguments (rc={rc})")
+    return out
+
+
+def eig_sym3(c6):
+    """Jacobi eigen-decomposition of one packed symmetric 3x3: (w ascending,
+    V with eigenvectors as columns)."""
+    a = np.ascontiguousarray(c6, dtype=np.float64).reshape(6)
+    w = np.empty(3, np.float64)
+    V = np.empty((3, 3), np.float64)
+    _load().oracle_eig_sym3(_ptr(a), _ptr(w), _ptr(V))
+    return w, V
+
+
+def unpack6(c6) -> np.ndarray:
+    """[...,6] packed upper triangle -> [...,3,3] symmetric matrices."""
+    c6 = np.asarray(c6)
+    xx, xy, xz, yy, yz, zz = (c6[..., i] for i in range(6))
+    return np.stack(
+        [np.stack([xx, xy, xz], -1), np.stack([xy, yy, yz], -1), np.stack([xz, yz, zz], -1)], -2
+    )

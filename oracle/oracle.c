@@ -1,0 +1,474 @@
+/*
+ * CPU oracle for the nearest-points search and per-point covariance step of
+ * GICP-style scan registration (Sec. III-C1 "Efficient registration method",
+ * Eq. 18-20; the step moved to the GPU in Sec. III-C1 and Sec. IV-E1).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the slow, plain definition that the
+ * CUDA path is checked against.  Only the test-suite, the smoke check and the
+ * benchmark's CPU-baseline leg may load it; the product library never does,
+ * and the two share no source, header, table or helper.
+ *
+ * What it computes (the per-point Gaussians N(p_i, C_i) of Eq. 19 need, for
+ * every query point, its k nearest points in the target cloud and the 3x3
+ * covariance of that neighbourhood):
+ *
+ *   d2(q,p)  = fmaf(dz,dz, fmaf(dy,dy, dx*dx)),  dx = q.x - p.x (binary32,
+ *              round to nearest, no contraction) -- the pinned order.
+ *   kNN(q)   = the first k target indices under the key (d2, index)
+ *              ascending: ties go to the lower index.
+ *   C        = (1/k) sum_j (p_j - mu)(p_j - mu)^T, mu = (1/k) sum_j p_j, in
+ *              binary64 from the binary32 inputs.
+ *   C'       = V diag(1,1,eps) V^T = I - (1 - eps) n n^T, n the unit
+ *              eigenvector of the smallest eigenvalue of C (cyclic Jacobi in
+ *              binary64); eps < 0 returns C itself.  If tr(C) <= 1e-20 the
+ *              neighbourhood is a single point and n := e_z.
+ *
+ * Two kNN forms: brute force (the definition itself) and a median-split k-d
+ * tree whose pruning bound is a proven lower bound on the binary32 d2, so it
+ * returns exactly the brute-force answer.
+ *
+ * Build: gcc -O2 -ffp-contract=off -fPIC -shared -pthread (no fast-math: the
+ * d2 order must not be re-associated or fused any further).
+ */
+#include <math.h>
+#include <pthread.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#include <unistd.h>
+
+/* ------------------------------------------------------------------ */
+/* The pinned binary32 squared distance.                               */
+/* ------------------------------------------------------------------ */
+static float sqdist(const float *q, const float *p)
+{
+    float dx = q[0] - p[0];
+    float dy = q[1] - p[1];
+    float dz = q[2] - p[2];
+    float sx = dx * dx; /* a separate, rounded product */
+    return fmaf(dz, dz, fmaf(dy, dy, sx));
+}
+
+/* (d2, idx) lexicographic order: does (da, ia) come strictly before (db, ib)? */
+static int key_less(float da, int32_t ia, float db, int32_t ib)
+{
+    if (da < db) return 1;
+    if (da > db) return 0;
+    return ia < ib;
+}
+
+/* A bounded list of the best k entries, kept sorted ascending by key. */
+typedef struct {
+    int k, n;
+    float *d;
+    int32_t *i;
+} bestlist;
+
+static void best_offer(bestlist *b, float d, int32_t idx)
+{
+    if (b->n == b->k && !key_less(d, idx, b->d[b->k - 1], b->i[b->k - 1]))
+        return;
+    int pos = (b->n < b->k) ? b->n : b->k - 1;
+    /* shift larger keys one slot towards the end */
+    while (pos > 0 && key_less(d, idx, b->d[pos - 1], b->i[pos - 1])) {
+        b->d[pos] = b->d[pos - 1];
+        b->i[pos] = b->i[pos - 1];
+        pos--;
+    }
+    b->d[pos] = d;
+    b->i[pos] = idx;
+    if (b->n < b->k) b->n++;
+}
+
+/* ------------------------------------------------------------------ */
+/* Thread fan-out over query blocks.                                   */
+/* ------------------------------------------------------------------ */
+typedef void (*range_fn)(void *ctx, int64_t lo, int64_t hi);
+typedef struct {
+    range_fn fn;
+    void *ctx;
+    int64_t lo, hi;
+} range_job;
+
+static void *range_thread(void *arg)
+{
+    range_job *j = (range_job *)arg;
+    j->fn(j->ctx, j->lo, j->hi);
+    return NULL;
+}
+
+int oracle_default_threads(void)
+{
+    long n = sysconf(_SC_NPROCESSORS_ONLN);
+    return n > 0 ? (int)n : 1;
+}
+
+static void parallel_for(int64_t n, int nthreads, range_fn fn, void *ctx)
+{
+    if (nthreads <= 0) nthreads = oracle_default_threads();
+    if (nthreads > 256) nthreads = 256;
+    if ((int64_t)nthreads > n) nthreads = (int)(n > 0 ? n : 1);
+    if (nthreads <= 1) {
+        fn(ctx, 0, n);
+        return;
+    }
+    pthread_t th[256];
+    range_job jobs[256];
+    int64_t chunk = (n + nthreads - 1) / nthreads;
+    int started = 0;
+    for (int t = 0; t < nthreads; t++) {
+        int64_t lo = t * chunk, hi = lo + chunk;
+        if (lo >= n) break;
+        if (hi > n) hi = n;
+        jobs[t].fn = fn;
+        jobs[t].ctx = ctx;
+        jobs[t].lo = lo;
+        jobs[t].hi = hi;
+        if (pthread_create(&th[t], NULL, range_thread, &jobs[t]) != 0) {
+            fn(ctx, lo, hi); /* run inline if a thread cannot start */
+            jobs[t].fn = NULL;
+        }
+        started = t + 1;
+    }
+    for (int t = 0; t < started; t++)
+        if (jobs[t].fn) pthread_join(th[t], NULL);
+}
+
+/* ------------------------------------------------------------------ */
+/* Brute-force kNN: the definition.                                    */
+/* ------------------------------------------------------------------ */
+typedef struct {
+    const float *q, *p;
+    int64_t m;
+    int k;
+    int32_t *idx;
+    float *d2;
+} brute_ctx;
+
+static void brute_range(void *vctx, int64_t lo, int64_t hi)
+{
+    brute_ctx *c = (brute_ctx *)vctx;
+    float *bd = (float *)malloc(sizeof(float) * c->k);
+    int32_t *bi = (int32_t *)malloc(sizeof(int32_t) * c->k);
+    for (int64_t n = lo; n < hi; n++) {
+        bestlist b = {c->k, 0, bd, bi};
+        const float *q = c->q + 3 * n;
+        for (int64_t j = 0; j < c->m; j++)
+            best_offer(&b, sqdist(q, c->p + 3 * j), (int32_t)j);
+        for (int r = 0; r < c->k; r++) {
+            c->idx[n * c->k + r] = bi[r];
+            c->d2[n * c->k + r] = bd[r];
+        }
+    }
+    free(bd);
+    free(bi);
+}
+
+/* q: [n,3] f32, p: [m,3] f32 -> idx [n,k] i32, d2 [n,k] f32.  Returns 0 on
+ * success, -1 on bad arguments (k < 1 or k > m). */
+int oracle_knn_brute(const float *q, int64_t n, const float *p, int64_t m, int k,
+                     int32_t *idx, float *d2, int nthreads)
+{
+    if (k < 1 || (int64_t)k > m || n < 0) return -1;
+    brute_ctx c = {q, p, m, k, idx, d2};
+    parallel_for(n, nthreads, brute_range, &c);
+    return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* Median-split k-d tree.                                              */
+/* ------------------------------------------------------------------ */
+#define KD_LEAF 8
+
+typedef struct {
+    int axis;       /* -1 for a leaf */
+    float split;    /* left holds coord <= split, right holds coord >= split */
+    int32_t left, right;  /* child node ids */
+    int64_t lo, hi;       /* leaf: range into perm */
+} kdnode;
+
+typedef struct {
+    const float *p; /* caller's points, kept by reference */
+    int64_t m;
+    int32_t *perm;
+    kdnode *nodes;
+    int64_t nnodes, cap;
+} kdtree;
+
+static float coord(const kdtree *t, int32_t i, int a) { return t->p[3 * (int64_t)i + a]; }
+
+/* Hoare-style quickselect on perm[lo,hi) by coordinate a so that position
+ * mid holds the median value, everything before it is <= and everything
+ * after it is >=. */
+static void kd_select(kdtree *t, int64_t lo, int64_t hi, int64_t mid, int a)
+{
+    while (hi - lo > 1) {
+        float pivot = coord(t, t->perm[lo + (hi - lo) / 2], a);
+        int64_t i = lo, j = hi - 1;
+        while (i <= j) {
+            while (coord(t, t->perm[i], a) < pivot) i++;
+            while (coord(t, t->perm[j], a) > pivot) j--;
+            if (i <= j) {
+                int32_t tmp = t->perm[i];
+                t->perm[i] = t->perm[j];
+                t->perm[j] = tmp;
+                i++;
+                j--;
+            }
+        }
+        /* now [lo, j] <= pivot, [i, hi) >= pivot, (j, i) == pivot */
+        if (mid <= j)
+            hi = j + 1;
+        else if (mid >= i)
+            lo = i;
+        else
+            return;
+    }
+}
+
+static int32_t kd_new_node(kdtree *t)
+{
+    if (t->nnodes == t->cap) {
+        t->cap = t->cap ? 2 * t->cap : 1024;
+        t->nodes = (kdnode *)realloc(t->nodes, sizeof(kdnode) * t->cap);
+    }
+    return (int32_t)t->nnodes++;
+}
+
+static int32_t kd_build_rec(kdtree *t, int64_t lo, int64_t hi)
+{
+    int32_t id = kd_new_node(t);
+    if (hi - lo <= KD_LEAF) {
+        kdnode leaf = {-1, 0.0f, -1, -1, lo, hi};
+        t->nodes[id] = leaf;
+        return id;
+    }
+    float mn[3], mx[3];
+    for (int a = 0; a < 3; a++) mn[a] = mx[a] = coord(t, t->perm[lo], a);
+    for (int64_t i = lo + 1; i < hi; i++)
+        for (int a = 0; a < 3; a++) {
+            float v = coord(t, t->perm[i], a);
+            if (v < mn[a]) mn[a] = v;
+            if (v > mx[a]) mx[a] = v;
+        }
+    int axis = 0;
+    for (int a = 1; a < 3; a++)
+        if (mx[a] - mn[a] > mx[axis] - mn[axis]) axis = a;
+    int64_t mid = lo + (hi - lo) / 2;
+    kd_select(t, lo, hi, mid, axis);
+    float split = coord(t, t->perm[mid], axis);
+    /* left = [lo, mid), right = [mid, hi): left coords <= split <= right */
+    int32_t l = kd_build_rec(t, lo, mid);
+    int32_t r = kd_build_rec(t, mid, hi);
+    kdnode in = {axis, split, l, r, lo, hi};
+    t->nodes[id] = in;
+    return id;
+}
+
+void *oracle_kdtree_build(const float *p, int64_t m)
+{
+    if (m < 1) return NULL;
+    kdtree *t = (kdtree *)calloc(1, sizeof(kdtree));
+    t->p = p;
+    t->m = m;
+    t->perm = (int32_t *)malloc(sizeof(int32_t) * m);
+    for (int64_t i = 0; i < m; i++) t->perm[i] = (int32_t)i;
+    kd_build_rec(t, 0, m);
+    return t;
+}
+
+void oracle_kdtree_free(void *vt)
+{
+    kdtree *t = (kdtree *)vt;
+    if (!t) return;
+    free(t->perm);
+    free(t->nodes);
+    free(t);
+}
+
+static void kd_search(const kdtree *t, int32_t id, const float *q, bestlist *b)
+{
+    const kdnode *nd = &t->nodes[id];
+    if (nd->axis < 0) {
+        for (int64_t i = nd->lo; i < nd->hi; i++) {
+            int32_t j = t->perm[i];
+            best_offer(b, sqdist(q, t->p + 3 * (int64_t)j), j);
+        }
+        return;
+    }
+    float qa = q[nd->axis];
+    int32_t near = (qa <= nd->split) ? nd->left : nd->right;
+    int32_t far = (qa <= nd->split) ? nd->right : nd->left;
+    kd_search(t, near, q, b);
+    /* Every far-side point p has |fl(q_a - p_a)| >= |fl(q_a - split)| by
+     * monotone rounding, and the binary32 d2 is a rounded sum of
+     * non-negative terms, so fl(s*s) bounds its d2 from below.  Ties must
+     * still be visited (a lower index may win), hence <=. */
+    float s = qa - nd->split;
+    float lb = s * s;
+    if (b->n < b->k || lb <= b->d[b->k - 1]) kd_search(t, far, q, b);
+}
+
+typedef struct {
+    const kdtree *t;
+    const float *q;
+    int k;
+    int32_t *idx;
+    float *d2;
+} kdq_ctx;
+
+static void kdq_range(void *vctx, int64_t lo, int64_t hi)
+{
+    kdq_ctx *c = (kdq_ctx *)vctx;
+    float *bd = (float *)malloc(sizeof(float) * c->k);
+    int32_t *bi = (int32_t *)malloc(sizeof(int32_t) * c->k);
+    for (int64_t n = lo; n < hi; n++) {
+        bestlist b = {c->k, 0, bd, bi};
+        kd_search(c->t, 0, c->q + 3 * n, &b);
+        for (int r = 0; r < c->k; r++) {
+            c->idx[n * c->k + r] = bi[r];
+            c->d2[n * c->k + r] = bd[r];
+        }
+    }
+    free(bd);
+    free(bi);
+}
+
+int oracle_kdtree_knn(void *vt, const float *q, int64_t n, int k, int32_t *idx, float *d2,
+                      int nthreads)
+{
+    kdtree *t = (kdtree *)vt;
+    if (!t || k < 1 || (int64_t)k > t->m || n < 0) return -1;
+    kdq_ctx c = {t, q, k, idx, d2};
+    parallel_for(n, nthreads, kdq_range, &c);
+    return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* Symmetric 3x3 eigen-decomposition by cyclic Jacobi rotations.        */
+/* ------------------------------------------------------------------ */
+/* a6 = (xx, xy, xz, yy, yz, zz).  On return w[0..2] are the eigenvalues
+ * (ascending) and V (row-major 3x3) holds the matching unit eigenvectors as
+ * its COLUMNS.  Each rotation zeroes one off-diagonal entry a_pq exactly
+ * (Jacobi's method, Golub & Van Loan sec. 8.5); sweeps repeat until the
+ * off-diagonal mass is negligible. */
+void oracle_eig_sym3(const double *a6, double *w, double *V)
+{
+    double A[3][3] = {{a6[0], a6[1], a6[2]}, {a6[1], a6[3], a6[4]}, {a6[2], a6[4], a6[5]}};
+    double Q[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
+    for (int sweep = 0; sweep < 64; sweep++) {
+        double off = A[0][1] * A[0][1] + A[0][2] * A[0][2] + A[1][2] * A[1][2];
+        double diag = A[0][0] * A[0][0] + A[1][1] * A[1][1] + A[2][2] * A[2][2];
+        if (off == 0.0 || off <= 1e-36 * diag) break;
+        for (int p = 0; p < 2; p++)
+            for (int q = p + 1; q < 3; q++) {
+                double apq = A[p][q];
+                if (apq == 0.0) continue;
+                /* choose the rotation angle so that the new a_pq is zero */
+                double theta = (A[q][q] - A[p][p]) / (2.0 * apq);
+                double t = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+                double c = 1.0 / sqrt(t * t + 1.0);
+                double s = t * c;
+                /* A <- J^T A J with J the (p,q) plane rotation */
+                for (int r = 0; r < 3; r++) {
+                    double arp = A[r][p], arq = A[r][q];
+                    A[r][p] = c * arp - s * arq;
+                    A[r][q] = s * arp + c * arq;
+                }
+                for (int r = 0; r < 3; r++) {
+                    double apr = A[p][r], aqr = A[q][r];
+                    A[p][r] = c * apr - s * aqr;
+                    A[q][r] = s * apr + c * aqr;
+                }
+                for (int r = 0; r < 3; r++) {
+                    double qrp = Q[r][p], qrq = Q[r][q];
+                    Q[r][p] = c * qrp - s * qrq;
+                    Q[r][q] = s * qrp + c * qrq;
+                }
+            }
+    }
+    /* sort ascending, permuting eigenvector columns along */
+    int order[3] = {0, 1, 2};
+    for (int i = 0; i < 3; i++)
+        for (int j = i + 1; j < 3; j++)
+            if (A[order[j]][order[j]] < A[order[i]][order[i]]) {
+                int tmp = order[i];
+                order[i] = order[j];
+                order[j] = tmp;
+            }
+    for (int i = 0; i < 3; i++) {
+        w[i] = A[order[i]][order[i]];
+        for (int r = 0; r < 3; r++) V[3 * r + i] = Q[r][order[i]];
+    }
+}
+
+/* ------------------------------------------------------------------ */
+/* Neighbourhood covariance in binary64.                               */
+/* ------------------------------------------------------------------ */
+/* One neighbourhood: points p[idx[j]], j < k.  Writes the 6 upper-triangle
+ * entries (xx, xy, xz, yy, yz, zz) of C (eps < 0) or of C' (eps >= 0). */
+void oracle_cov_one(const float *p, const int32_t *nb, int k, double eps, double *out)
+{
+    double mu[3] = {0, 0, 0};
+    for (int j = 0; j < k; j++)
+        for (int a = 0; a < 3; a++) mu[a] += (double)p[3 * (int64_t)nb[j] + a];
+    for (int a = 0; a < 3; a++) mu[a] /= (double)k;
+    double C[6] = {0, 0, 0, 0, 0, 0};
+    for (int j = 0; j < k; j++) {
+        double d[3];
+        for (int a = 0; a < 3; a++) d[a] = (double)p[3 * (int64_t)nb[j] + a] - mu[a];
+        C[0] += d[0] * d[0];
+        C[1] += d[0] * d[1];
+        C[2] += d[0] * d[2];
+        C[3] += d[1] * d[1];
+        C[4] += d[1] * d[2];
+        C[5] += d[2] * d[2];
+    }
+    for (int e = 0; e < 6; e++) C[e] /= (double)k;
+    if (eps < 0) {
+        memcpy(out, C, sizeof(C));
+        return;
+    }
+    double n[3] = {0, 0, 1};
+    if (C[0] + C[3] + C[5] > 1e-20) {
+        double w[3], V[9];
+        oracle_eig_sym3(C, w, V);
+        for (int r = 0; r < 3; r++) n[r] = V[3 * r + 0];
+        double nn = sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+        for (int r = 0; r < 3; r++) n[r] /= nn;
+    }
+    double f = 1.0 - eps;
+    out[0] = 1.0 - f * n[0] * n[0];
+    out[1] = -f * n[0] * n[1];
+    out[2] = -f * n[0] * n[2];
+    out[3] = 1.0 - f * n[1] * n[1];
+    out[4] = -f * n[1] * n[2];
+    out[5] = 1.0 - f * n[2] * n[2];
+}
+
+typedef struct {
+    const float *p;
+    const int32_t *idx;
+    int k;
+    double eps;
+    double *cov;
+} cov_ctx;
+
+static void cov_range(void *vctx, int64_t lo, int64_t hi)
+{
+    cov_ctx *c = (cov_ctx *)vctx;
+    for (int64_t n = lo; n < hi; n++)
+        oracle_cov_one(c->p, c->idx + n * c->k, c->k, c->eps, c->cov + 6 * n);
+}
+
+/* p: [m,3] f32 target, idx: [n,k] neighbour rows -> cov [n,6] f64. */
+int oracle_cov(const float *p, int64_t m, const int32_t *idx, int64_t n, int k, double eps,
+               double *cov, int nthreads)
+{
+    if (k < 1 || n < 0) return -1;
+    for (int64_t i = 0; i < n * (int64_t)k; i++)
+        if (idx[i] < 0 || (int64_t)idx[i] >= m) return -2;
+    cov_ctx c = {p, idx, k, eps, cov};
+    parallel_for(n, nthreads, cov_range, &c);
+    return 0;
+}
