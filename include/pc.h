@@ -1,0 +1,186 @@
+/*
+ * pc.h -- C ABI of the GB300 nearest-points + covariance library (libpc.so).
+ *
+ * The operation is the data-parallel step of GICP-style scan registration
+ * (Sec. III-C1 "Efficient registration method", Eq. 18-20): every point is
+ * modelled as a Gaussian N(p_i, C_i), and C_i is estimated from the point's
+ * k nearest neighbours in a target cloud or map.  The paper names "finding
+ * corresponding points and computing covariance" as the CPU bottleneck and
+ * moves both to the GPU (Sec. III-C1, Fig. 5; Sec. IV-E1); the map side is
+ * held in a "GPU-hash data structure" (Sec. III-C3 "Scan match for
+ * correction").
+ *
+ * Conventions shared by every call:
+ *  - Points are float32 [n,3] row-major (x, y, z), contiguous.
+ *  - Indices are 0-based positions in the caller's target array.
+ *  - idx is int32 [N,k], d2 is float32 [N,k], both ascending by the key
+ *    (d2, index): ties go to the lower index.  d2 is the binary32 value
+ *    fmaf(dz,dz, fmaf(dy,dy, dx*dx)), dx = q.x - p.x, bit-exact.
+ *  - cov is float32 [N,6] = (xx, xy, xz, yy, yz, zz) of
+ *    C = (1/k) sum_j (p_j - mu)(p_j - mu)^T over the k neighbours; with
+ *    eps >= 0 it is the plane-regularised V diag(1,1,eps) V^T, V the
+ *    eigenvectors of C ordered by decreasing eigenvalue, i.e.
+ *    I - (1-eps) n n^T with n the unit normal (smallest eigenvalue).
+ *  - "_dev" pointers are device memory (cudaMalloc / torch CUDA tensors);
+ *    the caller owns them.  A host or unregistered pointer where device
+ *    memory is required returns PC_ERR_BAD_POINTER.
+ *  - Every call except pc_build_target and pc_knn_cov_host is asynchronous
+ *    on the given stream (a cudaStream_t cast to void*; NULL = the legacy
+ *    default stream).  Argument errors are returned synchronously and
+ *    nothing is launched.  Conditions found on the device (a non-finite
+ *    query, a search past the configured limit, an out-of-range index given
+ *    to pc_cov) set bits in the target's status word: the affected rows get
+ *    idx = -1, d2 = +inf, cov = NaN, and pc_sync_status reports them.
+ *  - No call throws, traps or aborts.
+ *  - One GPU; a target handle is bound to the device that was current when
+ *    it was built.
+ */
+#ifndef PC_H
+#define PC_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define PC_API __attribute__((visibility("default")))
+#else
+#define PC_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pc_target_s *pc_target; /* opaque, library-owned */
+typedef struct pc_batch_s *pc_batch;   /* opaque, library-owned */
+typedef void *pc_stream;               /* cudaStream_t */
+
+typedef enum {
+    PC_OK = 0,
+    PC_ERR_INVALID_ARG = 1,  /* k < 1, k > 64, N < 0, M < 1, M >= 2^31, NULL with N > 0 */
+    PC_ERR_K_GT_M = 2,       /* k larger than the target size */
+    PC_ERR_NONFINITE = 3,    /* NaN/inf in the target (build) or a query (status) */
+    PC_ERR_OOM = 4,          /* device allocation failed */
+    PC_ERR_CUDA = 5,         /* any other CUDA runtime error */
+    PC_ERR_SEARCH_LIMIT = 6, /* widening search hit max_box_cells with exhaustive = 0 */
+    PC_ERR_BAD_POINTER = 7,  /* host / unregistered pointer where device memory is required */
+    PC_ERR_BAD_INDEX = 8,    /* pc_cov got an index outside [0, M) */
+    PC_ERR_DESTROYED = 9     /* handle already destroyed */
+} pc_status;
+
+/* Target-build options (Sec. III-C3: the map is held in a GPU hash). */
+typedef struct {
+    float cell_size;   /* > 0: voxel edge h in the caller's units; <= 0: chosen so the
+                          mean points per occupied cell is about `occupancy` */
+    float occupancy;   /* target mean points per occupied cell for the automatic h; <= 0: 6 */
+    float hash_load;   /* open-addressing load factor in (0, 0.9]; <= 0: 0.5 */
+    int max_box_cells; /* the radius-widening search stops growing its cell box here; <= 0: 4096 */
+    int exhaustive;    /* past max_box_cells: 1 = exact scan of every occupied cell,
+                          0 = mark the row and report PC_ERR_SEARCH_LIMIT */
+} pc_build_opts;
+
+/* Launch shape of the search kernel.  None of these changes any result. */
+typedef struct {
+    int tile;          /* queries per warp work item, 1..32; <= 0: 32 */
+    int warps;         /* warps per block, 1..16; <= 0: 4 */
+    float rho_scale;   /* first search radius = rho_scale x the previous query's k-th
+                          distance (or the target's calibrated radius); <= 0: 1.15 */
+} pc_tune;
+
+/* What the built target looks like (for reporting and tuning). */
+typedef struct {
+    int64_t m;          /* target points */
+    int64_t ncells;     /* occupied cells */
+    int64_t table_cap;  /* hash slots */
+    float cell_size;    /* h */
+    float origin[3];    /* grid origin = bbox minimum */
+    float bbox_max[3];
+    int dims[3];        /* cells per axis */
+    int64_t device_bytes; /* device memory held by the handle */
+    float rho_hint[64]; /* calibrated first search radius for k = 1..64 (0 if k > M) */
+} pc_target_info;
+
+/* One scan of a batch: device pointers, caller-owned. */
+typedef struct {
+    const float *q_dev; /* [n,3] */
+    int64_t n;
+    int32_t *idx_dev;   /* [n,k] */
+    float *d2_dev;      /* [n,k] */
+    float *cov_dev;     /* [n,6], may be NULL to skip the covariance */
+} pc_scan;
+
+/* Fills *o with the defaults listed above. */
+PC_API void pc_default_build_opts(pc_build_opts *o);
+
+/* Builds the device-resident voxel-hash grid over the target xyz_dev[M,3]
+ * (Sec. III-C3 "GPU-hash data structure"): finite check and bounding box,
+ * cell keys, an LSD radix sort of (key, index), the occupied-cell table in an
+ * open-addressing hash, and cell-ordered float4 copies of the points.  The
+ * library copies the points; xyz_dev may be freed afterwards.  Synchronises
+ * `s` (it reads sizes back).  opts may be NULL (defaults).  Errors:
+ * PC_ERR_INVALID_ARG (M < 1 or M >= 2^31, NULL pointers), PC_ERR_BAD_POINTER,
+ * PC_ERR_NONFINITE (any NaN/inf coordinate; no handle is made), PC_ERR_OOM,
+ * PC_ERR_CUDA.  On success *out owns device memory until pc_destroy_target. */
+PC_API pc_status pc_build_target(const float *xyz_dev, int64_t M, const pc_build_opts *opts,
+                          pc_stream s, pc_target *out);
+
+/* Frees the handle.  NULL is a no-op.  Work still queued on a stream that
+ * uses the handle must have finished (synchronise first). */
+PC_API void pc_destroy_target(pc_target t);
+
+/* Sets the launch shape for later calls on t (NULL restores defaults). */
+PC_API pc_status pc_set_tune(pc_target t, const pc_tune *tune);
+
+PC_API pc_status pc_get_info(pc_target t, pc_target_info *info);
+
+/* k nearest target points of each query q_dev[N,3] (Sec. III-C1: "finding
+ * corresponding points"): idx_dev[N,k], d2_dev[N,k] as described above.
+ * 1 <= k <= 64 and k <= M, N >= 0 (N = 0 is a no-op). */
+PC_API pc_status pc_knn(pc_target t, const float *q_dev, int64_t N, int k, int32_t *idx_dev,
+                 float *d2_dev, pc_stream s);
+
+/* Covariance of each neighbourhood row idx_dev[N,k] over the target
+ * (Sec. III-C1: C_i of Eq. 19 "computing covariance"): cov_dev[N,6].  eps < 0
+ * returns the raw C; eps >= 0 the plane-regularised form.  An index outside
+ * [0, M) gives a NaN row and PC_ERR_BAD_INDEX in the status word. */
+PC_API pc_status pc_cov(pc_target t, const int32_t *idx_dev, int64_t N, int k, float eps,
+                 float *cov_dev, pc_stream s);
+
+/* pc_knn and pc_cov fused in one launch; identical results to the two calls. */
+PC_API pc_status pc_knn_cov(pc_target t, const float *q_dev, int64_t N, int k, float eps,
+                     int32_t *idx_dev, float *d2_dev, float *cov_dev, pc_stream s);
+
+/* pc_knn_cov from HOST buffers (pinned or pageable): copies q in, runs, copies
+ * idx/d2/cov out, and synchronises `s` before returning.  Device staging
+ * buffers are kept in the handle and grown on demand (PC_ERR_OOM if that
+ * fails).  Device-side conditions are returned directly (no separate
+ * pc_sync_status needed). */
+PC_API pc_status pc_knn_cov_host(pc_target t, const float *q_host, int64_t N, int k, float eps,
+                          int32_t *idx_host, float *d2_host, float *cov_host, pc_stream s);
+
+/* Synchronises `s`, returns and clears the target's status word: PC_OK, or
+ * the first of PC_ERR_NONFINITE, PC_ERR_SEARCH_LIMIT, PC_ERR_BAD_INDEX raised
+ * since the last call, or PC_ERR_CUDA if the stream reported an error. */
+PC_API pc_status pc_sync_status(pc_target t, pc_stream s);
+
+/* Batched form: many scans against one target in ONE persistent launch that
+ * pulls (scan, tile) work items from a device counter, replayed as a CUDA
+ * graph.  pc_batch_plan copies the scan table to the device; the pointers in
+ * `scans` must stay valid while the plan is used.  All scans share k and eps.
+ * Results are bit-identical to pc_knn_cov on each scan alone. */
+PC_API pc_status pc_batch_plan(pc_target t, const pc_scan *scans, int n_scans, int k, float eps,
+                        pc_batch *out);
+/* Runs the plan on `s`.  The first run on a stream captures a CUDA graph
+ * (counter reset + persistent kernel); later runs replay it. */
+PC_API pc_status pc_batch_run(pc_batch b, pc_stream s);
+PC_API void pc_batch_destroy(pc_batch b);
+
+PC_API const char *pc_status_string(pc_status st);
+
+/* Library version string, e.g. "pc 0.1 sm_103a". */
+PC_API const char *pc_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PC_H */

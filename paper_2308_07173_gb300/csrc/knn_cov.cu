@@ -1,0 +1,701 @@
+// Nearest-points search and neighbourhood covariance on sm_103a CUDA cores
+// (Sec. III-C1 "Efficient registration method": the per-point covariances
+// C_i of Eq. 19 need every point's k nearest neighbours and the covariance
+// of that neighbourhood -- the step the paper moves from CPU to GPU).
+//
+// One warp owns a tile of up to 32 queries and runs them one at a time:
+//
+//  1. Radius-driven box.  With a search radius rho (the previous query's
+//     k-th distance x rho_scale, or the target's calibrated radius), the
+//     cells from cell(q - rho) to cell(q + rho) on each axis are looked up
+//     in the voxel hash, one cell per lane, and their point ranges are
+//     prefix-summed across the warp.
+//  2. Candidates.  32 candidates at a time, one per lane, are read as
+//     coalesced float4 from the cell-sorted copy; each lane computes the
+//     pinned binary32 d2 and the 64-bit key (d2 bits << 32 | index), which
+//     orders exactly like (d2, index).
+//  3. Filter + top-k.  A candidate survives if d2 <= tau (the square of the
+//     radius the box is CERTIFIED to cover, see certified_tau) and it beats
+//     the current k-th key.  Survivors are staged in shared memory; every 32
+//     of them are bitonic-sorted across the warp with shuffles and merged
+//     into the register-resident top-k (lane l holds rank l, and rank 32+l
+//     for k > 32).
+//  4. Stop or widen.  If k survivors exist, every point outside the box or
+//     beyond tau is provably farther than the k-th, so the answer is exact.
+//     Otherwise rho grows and the box is scanned again; past max_box_cells
+//     an exact scan over all occupied cells (with per-cell lower bounds)
+//     takes over, or the row is marked PC_ERR_SEARCH_LIMIT.
+//  5. Epilogue (fused form).  Once the tile is done, lane i computes query
+//     i's covariance from the neighbour indices staged in shared memory:
+//     a two-pass binary32 mean/centred sum shifted by the nearest
+//     neighbour, then -- for eps >= 0 -- the closed-form symmetric 3x3
+//     eigen-solve and C' = I - (1-eps) n n^T.
+//
+// Everything is exact/deterministic by construction: the tile, the launch
+// shape, rho and the batching never change a result bit.
+#include <cmath>
+#include <cstdint>
+#include <mutex>
+
+#include "pc_device.cuh"
+#include "pc_internal.h"
+
+using namespace pcdev;
+
+namespace {
+
+typedef unsigned long long u64;
+
+__device__ __forceinline__ u64 umin64(u64 a, u64 b) { return a < b ? a : b; }
+__device__ __forceinline__ u64 umax64(u64 a, u64 b) { return a < b ? b : a; }
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+// Bitonic sort of one key per lane into DESCENDING lane order.
+__device__ __forceinline__ u64 sort32_desc(u64 x, int lane) {
+#pragma unroll
+    for (int size = 2; size <= 32; size <<= 1) {
+#pragma unroll
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            u64 y = __shfl_xor_sync(FULL, x, stride);
+            bool desc_block = (lane & size) == 0;  // all lanes at size 32
+            bool lower = (lane & stride) == 0;
+            x = (lower == desc_block) ? umax64(x, y) : umin64(x, y);
+        }
+    }
+    return x;
+}
+
+// Bitonic merge of a bitonic lane sequence into ASCENDING lane order.
+__device__ __forceinline__ u64 merge32_asc(u64 x, int lane) {
+#pragma unroll
+    for (int stride = 16; stride > 0; stride >>= 1) {
+        u64 y = __shfl_xor_sync(FULL, x, stride);
+        x = ((lane & stride) == 0) ? umin64(x, y) : umax64(x, y);
+    }
+    return x;
+}
+
+template <int SLOTS>
+struct SearchState {
+    u64 L[SLOTS];  // lane l: rank l (slot 0) and rank 32 + l (slot 1)
+    u64 kth;       // warp-uniform: the rank k-1 key, EMPTY_KEY until k exist
+    int npend;     // warp-uniform: survivors staged in shared memory
+};
+
+template <int SLOTS>
+__device__ __forceinline__ void state_reset(SearchState<SLOTS>& S) {
+#pragma unroll
+    for (int s = 0; s < SLOTS; ++s) S.L[s] = EMPTY_KEY;
+    S.kth = EMPTY_KEY;
+    S.npend = 0;
+}
+
+template <int SLOTS>
+__device__ __forceinline__ u64 topk_rank(const SearchState<SLOTS>& S, int r) {
+    u64 v = (SLOTS == 2 && r >= 32) ? S.L[SLOTS - 1] : S.L[0];
+    return __shfl_sync(FULL, v, r & 31);
+}
+
+// Merge 32 staged keys (one per lane, any order) into the sorted top list.
+// A ascending + B descending -> min(A, B) is bitonic and holds the smallest
+// |A| of A u B; for two slots the 64-list [L0, min(L1, c)] is bitonic.
+template <int SLOTS>
+__device__ __forceinline__ void topk_merge(SearchState<SLOTS>& S, u64 c, int k, int lane) {
+    c = sort32_desc(c, lane);
+    if (SLOTS == 1) {
+        S.L[0] = merge32_asc(umin64(S.L[0], c), lane);
+    } else {
+        u64 b = umin64(S.L[SLOTS - 1], c);
+        u64 lo = umin64(S.L[0], b), hi = umax64(S.L[0], b);
+        S.L[0] = merge32_asc(lo, lane);
+        S.L[SLOTS - 1] = merge32_asc(hi, lane);
+    }
+    S.kth = topk_rank(S, k - 1);
+}
+
+template <int SLOTS>
+__device__ __forceinline__ void offer(SearchState<SLOTS>& S, bool pass, u64 key, u64* pend, int k,
+                                      int lane) {
+    unsigned m = __ballot_sync(FULL, pass);
+    if (m == 0u) return;
+    if (pass) pend[S.npend + __popc(m & lanemask_lt())] = key;
+    S.npend += __popc(m);
+    __syncwarp();
+    if (S.npend >= 32) {
+        topk_merge(S, pend[lane], k, lane);
+        __syncwarp();
+        const int rest = S.npend - 32;
+        if (lane < rest) pend[lane] = pend[32 + lane];
+        __syncwarp();
+        S.npend = rest;
+    }
+}
+
+template <int SLOTS>
+__device__ __forceinline__ void flush(SearchState<SLOTS>& S, u64* pend, int k, int lane) {
+    if (S.npend > 0) {
+        u64 c = lane < S.npend ? pend[lane] : EMPTY_KEY;
+        topk_merge(S, c, k, lane);
+        S.npend = 0;
+    }
+    __syncwarp();
+}
+
+// One pass over up to 32 point ranges (one per lane): every point becomes a
+// candidate, 32 per step, each lane finding its owning range by a binary
+// search over the warp's exclusive prefix of counts.
+template <int SLOTS>
+__device__ __forceinline__ void scan_ranges(const Grid& g, float qx, float qy, float qz,
+                                            uint32_t start, uint32_t cnt, float tau,
+                                            SearchState<SLOTS>& S, u64* pend, int k, int lane) {
+    uint32_t incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t t = __shfl_up_sync(FULL, incl, o);
+        if (lane >= o) incl += t;
+    }
+    const uint32_t total = __shfl_sync(FULL, incl, 31);
+    const uint32_t excl = incl - cnt;
+    for (uint32_t cb = 0; cb < total; cb += 32) {
+        const uint32_t t = cb + lane;
+        int j = 0;
+#pragma unroll
+        for (int s = 16; s >= 1; s >>= 1) {
+            uint32_t e = __shfl_sync(FULL, excl, j + s);
+            if (e <= t) j += s;
+        }
+        const uint32_t st = __shfl_sync(FULL, start, j);
+        const uint32_t ej = __shfl_sync(FULL, excl, j);
+        bool pass = false;
+        u64 key = EMPTY_KEY;
+        if (t < total) {
+            const float4 p = __ldg(&g.pts[st + (t - ej)]);
+            const float d2 = sqdist_pinned(qx, qy, qz, p.x, p.y, p.z);
+            key = ((u64)__float_as_uint(d2) << 32) | (u64)__float_as_uint(p.w);
+            pass = (d2 <= tau) && (key < S.kth);
+        }
+        offer(S, pass, key, pend, k, lane);
+    }
+}
+
+// Distance from q to the nearer face of the cell slab [lo, hi] on one axis.
+__device__ __forceinline__ float slab_gap(float q, float o, int lo, int hi, float h) {
+    const float flo = o + (float)lo * h;
+    const float fhi = o + (float)(hi + 1) * h;
+    return fminf(q - flo, fhi - q);
+}
+
+// tau such that EVERY target point outside the cell box [l, h] has a binary32
+// d2 strictly greater than tau (or -1 if nothing can be certified).
+//
+// A point in a cell c' < l on some axis has fl(fl(p-o)*inv_h) < l, so
+// p < o + l*h*(1 + 3.01u) with u = 2^-24; symmetrically for c' > h.  The
+// face positions and the gap are computed with a few more roundings.  All
+// together the true distance to any outside point is at least
+// gap - 8u*(|o| + |q| + |c|*h), where the margin eta below is twice that.
+// The binary32 d2 of a point at true distance D is >= D^2 (1 - 5u), so
+// tau = Rs^2 (1 - 2^-20) with Rs = gap - eta is strictly below it.  For
+// Rs < 2^-60 nothing is certified (products could be subnormal).
+__device__ __forceinline__ float certified_tau(const Grid& g, float qx, float qy, float qz, int lx,
+                                               int hx, int ly, int hy, int lz, int hz) {
+    float R = fminf(slab_gap(qx, g.ox, lx, hx, g.h),
+                    fminf(slab_gap(qy, g.oy, ly, hy, g.h), slab_gap(qz, g.oz, lz, hz, g.h)));
+    int cm = max(max(max(abs(lx), abs(hx + 1)), max(abs(ly), abs(hy + 1))),
+                 max(abs(lz), abs(hz + 1)));
+    float qm = fmaxf(fabsf(qx), fmaxf(fabsf(qy), fabsf(qz)));
+    float eta = 0x1p-20f * (g.coord_scale + qm + (float)cm * g.h);
+    float Rs = R - eta;
+    if (!(Rs > 0x1p-60f)) return -1.0f;
+    return (Rs * Rs) * (1.0f - 0x1p-20f);
+}
+
+// Lower bound on the binary32 d2 from q to any point of cell (cx, cy, cz);
+// same margin argument as certified_tau.
+__device__ __forceinline__ float cell_lower_bound2(const Grid& g, float qx, float qy, float qz,
+                                                   int cx, int cy, int cz) {
+    float qm = fmaxf(fabsf(qx), fmaxf(fabsf(qy), fabsf(qz)));
+    int cm = max(cx, max(cy, cz)) + 1;
+    float eta = 0x1p-20f * (g.coord_scale + qm + (float)cm * g.h);
+    float s = 0.0f;
+    {
+        float lo = g.ox + (float)cx * g.h, hi = g.ox + (float)(cx + 1) * g.h;
+        float d = fmaxf(fmaxf(lo - qx, qx - hi), 0.0f) - eta;
+        if (d > 0.0f) s = s + d * d;
+    }
+    {
+        float lo = g.oy + (float)cy * g.h, hi = g.oy + (float)(cy + 1) * g.h;
+        float d = fmaxf(fmaxf(lo - qy, qy - hi), 0.0f) - eta;
+        if (d > 0.0f) s = s + d * d;
+    }
+    {
+        float lo = g.oz + (float)cz * g.h, hi = g.oz + (float)(cz + 1) * g.h;
+        float d = fmaxf(fmaxf(lo - qz, qz - hi), 0.0f) - eta;
+        if (d > 0.0f) s = s + d * d;
+    }
+    return s * (1.0f - 0x1p-20f);
+}
+
+template <int SLOTS>
+__device__ void scan_box(const Grid& g, float qx, float qy, float qz, int lx, int ly, int lz,
+                         int ex, int ey, int ez, float tau, SearchState<SLOTS>& S, u64* pend,
+                         int k, int lane) {
+    const int ncl = ex * ey * ez;
+    for (int base = 0; base < ncl; base += 32) {
+        const int c = base + lane;
+        uint32_t start = 0u, cnt = 0u;
+        if (c < ncl) {
+            const int cx = lx + c % ex;
+            const int r = c / ex;
+            const int cy = ly + r % ey;
+            const int cz = lz + r / ey;
+            const uint2 v = lookup_cell(g, pack_key(cx, cy, cz, g.bx, g.by));
+            start = v.x;
+            cnt = v.y;
+        }
+        scan_ranges(g, qx, qy, qz, start, cnt, tau, S, pend, k, lane);
+    }
+}
+
+template <int SLOTS>
+__device__ void scan_all_cells(const Grid& g, float qx, float qy, float qz, SearchState<SLOTS>& S,
+                               u64* pend, int k, int lane) {
+    const u64 mx = (1ull << g.bx) - 1ull, my = (1ull << g.by) - 1ull;
+    for (int64_t ub = 0; ub < g.ncells; ub += 32) {
+        const int64_t u = ub + lane;
+        uint32_t start = 0u, cnt = 0u;
+        if (u < g.ncells) {
+            const u64 key = g.cell_keys[u];
+            const int cx = (int)(key & mx), cy = (int)((key >> g.bx) & my),
+                      cz = (int)(key >> (g.bx + g.by));
+            const float lb2 = cell_lower_bound2(g, qx, qy, qz, cx, cy, cz);
+            const float kd = S.kth == EMPTY_KEY ? INFINITY : __uint_as_float((uint32_t)(S.kth >> 32));
+            if (lb2 <= kd) {
+                start = g.cell_start[u];
+                cnt = g.cell_start[u + 1] - start;
+            }
+        }
+        scan_ranges(g, qx, qy, qz, start, cnt, INFINITY, S, pend, k, lane);
+    }
+}
+
+// Exact k nearest neighbours of one query (warp-uniform control flow).
+// Returns false only when the search hit max_box_cells with exhaustive = 0.
+template <int SLOTS>
+__device__ bool knn_search(const Grid& g, float qx, float qy, float qz, int k, float& rho,
+                           SearchState<SLOTS>& S, u64* pend, int lane) {
+    for (int attempt = 0; attempt < 40; ++attempt) {
+        const int lx = cell_of(__fsub_rn(qx, rho), g.ox, g.inv_h);
+        const int hx = cell_of(__fadd_rn(qx, rho), g.ox, g.inv_h);
+        const int ly = cell_of(__fsub_rn(qy, rho), g.oy, g.inv_h);
+        const int hy = cell_of(__fadd_rn(qy, rho), g.oy, g.inv_h);
+        const int lz = cell_of(__fsub_rn(qz, rho), g.oz, g.inv_h);
+        const int hz = cell_of(__fadd_rn(qz, rho), g.oz, g.inv_h);
+        const float tau = certified_tau(g, qx, qy, qz, lx, hx, ly, hy, lz, hz);
+        const int cxl = max(lx, 0), cxh = min(hx, g.dimx - 1);
+        const int cyl = max(ly, 0), cyh = min(hy, g.dimy - 1);
+        const int czl = max(lz, 0), czh = min(hz, g.dimz - 1);
+        const int64_t ex = max(cxh - cxl + 1, 0), ey = max(cyh - cyl + 1, 0),
+                      ez = max(czh - czl + 1, 0);
+        const int64_t ncl = ex * ey * ez;
+        if (ncl > (int64_t)g.max_box_cells) break;
+        state_reset(S);
+        if (ncl > 0)
+            scan_box(g, qx, qy, qz, cxl, cyl, czl, (int)ex, (int)ey, (int)ez, tau, S, pend, k,
+                     lane);
+        flush(S, pend, k, lane);
+        if (S.kth != EMPTY_KEY) return true;
+        int found = 0;
+#pragma unroll
+        for (int s = 0; s < SLOTS; ++s) found += __popc(__ballot_sync(FULL, S.L[s] != EMPTY_KEY));
+        float f = 1.3f * sqrtf((float)k / (float)max(found, 1));
+        f = fminf(fmaxf(f, 1.5f), 4.0f);
+        rho = fminf(fmaxf(rho, 1e-3f * g.h) * f, 1e30f);
+    }
+    if (!g.exhaustive) return false;
+    state_reset(S);
+    scan_all_cells(g, qx, qy, qz, S, pend, k, lane);
+    flush(S, pend, k, lane);
+    return S.kth != EMPTY_KEY;
+}
+
+// ---------------------------------------------------------------- covariance
+__device__ __forceinline__ float3 cross3(float3 a, float3 b) {
+    return make_float3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+__device__ __forceinline__ float dot3(float3 a, float3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+
+// Unit eigenvector of the smallest eigenvalue of a symmetric 3x3 matrix.
+// Eigenvalues by the trigonometric closed form for symmetric 3x3 matrices
+// (O. K. Smith, CACM 4(4), 1961): with q = tr/3, p^2 = ||A - qI||_F^2 / 6 and
+// r = det((A - qI)/p)/2, lambda = q + 2p cos(acos(r)/3 + 2 pi j/3); j = 1 is
+// the smallest.  The eigenvector is the largest cross product of two rows of
+// A - lambda_min I (the stable choice discussed by J. Kopp, "Efficient
+// numerical diagonalization of hermitian 3x3 matrices", 2008); when those
+// rows have rank <= 1 (lambda_min repeated) any unit vector orthogonal to
+// the largest row is an eigenvector; a zero or isotropic matrix gives e_z.
+// The matrix is first scaled by an exact power of two so its largest entry
+// lies in [0.5, 1).
+__device__ float3 min_eigvec(float a00, float a01, float a02, float a11, float a12, float a22) {
+    const float amax = fmaxf(fmaxf(fabsf(a00), fabsf(a11)),
+                             fmaxf(fabsf(a22), fmaxf(fmaxf(fabsf(a01), fabsf(a02)), fabsf(a12))));
+    if (!(amax > 0.0f) || !isfinite(amax)) return make_float3(0.0f, 0.0f, 1.0f);
+    int e;
+    frexpf(amax, &e);
+    const float sc = ldexpf(1.0f, -e);
+    a00 *= sc; a01 *= sc; a02 *= sc; a11 *= sc; a12 *= sc; a22 *= sc;
+    const float q = (a00 + a11 + a22) / 3.0f;
+    const float b00 = a00 - q, b11 = a11 - q, b22 = a22 - q;
+    const float p1 = a01 * a01 + a02 * a02 + a12 * a12;
+    const float p2 = b00 * b00 + b11 * b11 + b22 * b22 + 2.0f * p1;
+    if (!(p2 > 0.0f)) return make_float3(0.0f, 0.0f, 1.0f);
+    const float p = sqrtf(p2 / 6.0f);
+    const float ip = 1.0f / p;
+    const float c00 = b00 * ip, c11 = b11 * ip, c22 = b22 * ip;
+    const float c01 = a01 * ip, c02 = a02 * ip, c12 = a12 * ip;
+    const float det = c00 * (c11 * c22 - c12 * c12) - c01 * (c01 * c22 - c12 * c02) +
+                      c02 * (c01 * c12 - c11 * c02);
+    const float r = fminf(fmaxf(0.5f * det, -1.0f), 1.0f);
+    const float phi = acosf(r) / 3.0f;
+    const float lmin = q + 2.0f * p * cosf(phi + 2.09439510239319549f);
+    const float3 r0 = make_float3(a00 - lmin, a01, a02);
+    const float3 r1 = make_float3(a01, a11 - lmin, a12);
+    const float3 r2 = make_float3(a02, a12, a22 - lmin);
+    float3 best = cross3(r0, r1);
+    float db = dot3(best, best);
+    {
+        const float3 x = cross3(r0, r2);
+        const float d = dot3(x, x);
+        if (d > db) { best = x; db = d; }
+    }
+    {
+        const float3 x = cross3(r1, r2);
+        const float d = dot3(x, x);
+        if (d > db) { best = x; db = d; }
+    }
+    if (db > 1e-24f) {
+        const float inv = 1.0f / sqrtf(db);
+        return make_float3(best.x * inv, best.y * inv, best.z * inv);
+    }
+    float3 rm = r0;
+    float nm = dot3(r0, r0);
+    {
+        const float d = dot3(r1, r1);
+        if (d > nm) { rm = r1; nm = d; }
+    }
+    {
+        const float d = dot3(r2, r2);
+        if (d > nm) { rm = r2; nm = d; }
+    }
+    if (nm > 1e-24f) {
+        const float ax = fabsf(rm.x), ay = fabsf(rm.y), az = fabsf(rm.z);
+        const float3 ea = (ax <= ay && ax <= az) ? make_float3(1.0f, 0.0f, 0.0f)
+                          : (ay <= az ? make_float3(0.0f, 1.0f, 0.0f) : make_float3(0.0f, 0.0f, 1.0f));
+        const float3 v = cross3(rm, ea);
+        const float inv = 1.0f / sqrtf(dot3(v, v));
+        return make_float3(v.x * inv, v.y * inv, v.z * inv);
+    }
+    return make_float3(0.0f, 0.0f, 1.0f);
+}
+
+// Covariance of one neighbourhood row (Sec. III-C1, C_i of Eq. 19).
+// Two passes in binary32, both shifted by the first (nearest) neighbour p0
+// so the sums stay small: mean m of (p_j - p0), then the centred moments of
+// (p_j - p0) - m, divided by k.  Built with --fmad=false, so every + and *
+// below is rounded once and the fused and standalone kernels agree bit for
+// bit.  `check`: validate every index (pc_cov); otherwise a leading -1
+// marks an unanswered row.
+__device__ void cov_row(const Grid& g, const int32_t* nb, int k, float eps, float* out,
+                        bool check) {
+    bool bad = nb[0] < 0;
+    if (check) {
+        bool oob = false;
+        for (int j = 0; j < k; ++j) oob |= (nb[j] < 0) || ((int64_t)nb[j] >= g.m);
+        if (oob) atomicOr(g.status, ST_BAD_INDEX);
+        bad = oob;
+    }
+    if (bad) {
+        const float nan = __int_as_float(0x7fc00000);
+        for (int e = 0; e < 6; ++e) out[e] = nan;
+        return;
+    }
+    const float4 p0 = __ldg(&g.xyz[nb[0]]);
+    float sx = 0.0f, sy = 0.0f, sz = 0.0f;
+    for (int j = 0; j < k; ++j) {
+        const float4 p = __ldg(&g.xyz[nb[j]]);
+        sx = sx + (p.x - p0.x);
+        sy = sy + (p.y - p0.y);
+        sz = sz + (p.z - p0.z);
+    }
+    const float fk = (float)k;
+    const float mx = sx / fk, my = sy / fk, mz = sz / fk;
+    float cxx = 0.0f, cxy = 0.0f, cxz = 0.0f, cyy = 0.0f, cyz = 0.0f, czz = 0.0f;
+    for (int j = 0; j < k; ++j) {
+        const float4 p = __ldg(&g.xyz[nb[j]]);
+        const float dx = (p.x - p0.x) - mx;
+        const float dy = (p.y - p0.y) - my;
+        const float dz = (p.z - p0.z) - mz;
+        cxx = __fmaf_rn(dx, dx, cxx);
+        cxy = __fmaf_rn(dx, dy, cxy);
+        cxz = __fmaf_rn(dx, dz, cxz);
+        cyy = __fmaf_rn(dy, dy, cyy);
+        cyz = __fmaf_rn(dy, dz, cyz);
+        czz = __fmaf_rn(dz, dz, czz);
+    }
+    cxx = cxx / fk; cxy = cxy / fk; cxz = cxz / fk;
+    cyy = cyy / fk; cyz = cyz / fk; czz = czz / fk;
+    if (eps < 0.0f) {
+        out[0] = cxx; out[1] = cxy; out[2] = cxz; out[3] = cyy; out[4] = cyz; out[5] = czz;
+        return;
+    }
+    const float3 n = min_eigvec(cxx, cxy, cxz, cyy, cyz, czz);
+    const float f = 1.0f - eps;
+    out[0] = 1.0f - f * n.x * n.x;
+    out[1] = -f * n.x * n.y;
+    out[2] = -f * n.x * n.z;
+    out[3] = 1.0f - f * n.y * n.y;
+    out[4] = -f * n.y * n.z;
+    out[5] = 1.0f - f * n.z * n.z;
+}
+
+// ---------------------------------------------------------------- tiles
+struct TileArgs {
+    int k;
+    float eps;
+    float rho_scale;
+};
+
+// Per-warp shared memory: 64 staged survivor keys, then (fused form) the
+// tile's neighbour indices, row stride k|1 (odd, so the epilogue's
+// lane-per-row reads hit distinct banks).
+__host__ __device__ __forceinline__ int idx_stride(int k) { return k | 1; }
+__host__ __device__ __forceinline__ size_t warp_smem_bytes(int k, bool cov) {
+    size_t b = 64 * sizeof(u64);
+    if (cov) b += (size_t)32 * idx_stride(k) * sizeof(int32_t);
+    return (b + 15) & ~(size_t)15;
+}
+
+template <int SLOTS, bool COV>
+__device__ void process_tile(const Grid& g, const float* __restrict__ q, int64_t n0, int cnt,
+                             const TileArgs& a, int32_t* __restrict__ idx, float* __restrict__ d2,
+                             float* __restrict__ cov, float& rho, u64* pend, int32_t* sidx,
+                             int lane) {
+    const int k = a.k;
+    const int ks = idx_stride(k);
+    for (int i = 0; i < cnt; ++i) {
+        const int64_t n = n0 + i;
+        const float qx = __ldg(q + 3 * n), qy = __ldg(q + 3 * n + 1), qz = __ldg(q + 3 * n + 2);
+        const bool finite = isfinite(qx) && isfinite(qy) && isfinite(qz);
+        SearchState<SLOTS> S;
+        state_reset(S);
+        bool ok = false;
+        if (finite) ok = knn_search<SLOTS>(g, qx, qy, qz, k, rho, S, pend, lane);
+        if (!ok && lane == 0) atomicOr(g.status, finite ? ST_SEARCH_LIMIT : ST_NONFINITE);
+#pragma unroll
+        for (int s = 0; s < SLOTS; ++s) {
+            const int r = s * 32 + lane;
+            if (r < k) {
+                const u64 key = S.L[s];
+                const int32_t oi = ok ? (int32_t)(uint32_t)key : -1;
+                const float od = ok ? __uint_as_float((uint32_t)(key >> 32)) : INFINITY;
+                idx[n * k + r] = oi;
+                d2[n * k + r] = od;
+                if (COV) sidx[i * ks + r] = oi;
+            }
+        }
+        if (ok) {
+            const float dk = __uint_as_float((uint32_t)(S.kth >> 32));
+            rho = fminf(fmaxf(sqrtf(dk) * a.rho_scale, 1e-2f * g.h), 1e30f);
+        }
+    }
+    if (COV && cov != nullptr) {
+        __syncwarp();
+        if (lane < cnt) cov_row(g, sidx + lane * ks, k, a.eps, cov + 6 * (n0 + lane), false);
+        __syncwarp();
+    }
+}
+
+template <int SLOTS, bool COV>
+__global__ void __launch_bounds__(512) k_knn(Grid g, const float* __restrict__ q, int64_t N,
+                                             int tile, TileArgs a, float rho0,
+                                             int32_t* __restrict__ idx, float* __restrict__ d2,
+                                             float* __restrict__ cov) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nwarps = blockDim.x >> 5;
+    unsigned char* base = smem + (size_t)warp * warp_smem_bytes(a.k, COV);
+    u64* pend = reinterpret_cast<u64*>(base);
+    int32_t* sidx = reinterpret_cast<int32_t*>(base + 64 * sizeof(u64));
+    const int64_t t = (int64_t)blockIdx.x * nwarps + warp;
+    const int64_t n0 = t * tile;
+    if (n0 >= N) return;
+    const int cnt = (int)min((int64_t)tile, N - n0);
+    float rho = rho0;
+    process_tile<SLOTS, COV>(g, q, n0, cnt, a, idx, d2, cov, rho, pend, sidx, lane);
+}
+
+// Batched form: one persistent launch; warps pull (scan, tile) items from a
+// device counter over the scans' prefix-summed tile table.
+template <int SLOTS, bool COV>
+__global__ void __launch_bounds__(512) k_knn_batch(Grid g, const ScanDesc* __restrict__ scans,
+                                                   int nscans, int64_t total_tiles, int tile,
+                                                   TileArgs a, float rho0,
+                                                   unsigned long long* counter) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    unsigned char* base = smem + (size_t)warp * warp_smem_bytes(a.k, COV);
+    u64* pend = reinterpret_cast<u64*>(base);
+    int32_t* sidx = reinterpret_cast<int32_t*>(base + 64 * sizeof(u64));
+    float rho = rho0;
+    for (;;) {
+        unsigned long long item = 0;
+        if (lane == 0) item = atomicAdd(counter, 1ull);
+        item = __shfl_sync(FULL, item, 0);
+        if ((int64_t)item >= total_tiles) break;
+        int lo = 0, hi = nscans - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (scans[mid].tile0 <= (int64_t)item) lo = mid; else hi = mid - 1;
+        }
+        const ScanDesc sd = scans[lo];
+        const int64_t n0 = ((int64_t)item - sd.tile0) * tile;
+        const int cnt = (int)min((int64_t)tile, sd.n - n0);
+        process_tile<SLOTS, COV>(g, sd.q, n0, cnt, a, sd.idx, sd.d2, sd.cov, rho, pend, sidx, lane);
+    }
+}
+
+__global__ void k_cov(Grid g, const int32_t* __restrict__ idx, int64_t N, int k, float eps,
+                      float* __restrict__ cov) {
+    const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    cov_row(g, idx + n * k, k, eps, cov + 6 * n, true);
+}
+
+template <typename K>
+cudaError_t allow_smem(K kern) {
+    return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+}
+
+// Opt every search kernel into large dynamic shared memory, once per device
+// (outside any stream capture: the first launch or plan does it).
+std::mutex g_attr_mu;
+unsigned g_attr_done = 0u;
+cudaError_t ensure_attrs() {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const unsigned bit = 1u << (dev & 31);
+    std::lock_guard<std::mutex> lk(g_attr_mu);
+    if (g_attr_done & bit) return cudaSuccess;
+    if ((e = allow_smem(k_knn<1, true>)) != cudaSuccess) return e;
+    if ((e = allow_smem(k_knn<1, false>)) != cudaSuccess) return e;
+    if ((e = allow_smem(k_knn<2, true>)) != cudaSuccess) return e;
+    if ((e = allow_smem(k_knn<2, false>)) != cudaSuccess) return e;
+    if ((e = allow_smem(k_knn_batch<1, true>)) != cudaSuccess) return e;
+    if ((e = allow_smem(k_knn_batch<1, false>)) != cudaSuccess) return e;
+    if ((e = allow_smem(k_knn_batch<2, true>)) != cudaSuccess) return e;
+    if ((e = allow_smem(k_knn_batch<2, false>)) != cudaSuccess) return e;
+    g_attr_done |= bit;
+    return cudaSuccess;
+}
+
+int clamp_tile(int t) { return t <= 0 ? 32 : (t > 32 ? 32 : t); }
+int clamp_warps(int w) { return w <= 0 ? 4 : (w > 16 ? 16 : w); }
+
+}  // namespace
+
+// ---------------------------------------------------------------- host side
+cudaError_t pc_launch_knn(const pc_target_s* t, const float* q, int64_t N, int k, float eps,
+                          int32_t* idx, float* d2, float* cov, float rho0, cudaStream_t s) {
+    if (N == 0) return cudaSuccess;
+    const int tile = clamp_tile(t->tune.tile);
+    const int warps = clamp_warps(t->tune.warps);
+    TileArgs a{k, eps, t->tune.rho_scale > 0 ? t->tune.rho_scale : 1.15f};
+    const bool with_cov = cov != nullptr;
+    const size_t smem = (size_t)warps * warp_smem_bytes(k, with_cov);
+    const int64_t tiles = (N + tile - 1) / tile;
+    const int64_t blocks = (tiles + warps - 1) / warps;
+    const dim3 grid((unsigned)blocks), block(warps * 32);
+    cudaError_t e = ensure_attrs();
+    if (e != cudaSuccess) return e;
+    if (k <= 32) {
+        if (with_cov) {
+            k_knn<1, true><<<grid, block, smem, s>>>(t->g, q, N, tile, a, rho0, idx, d2, cov);
+        } else {
+            k_knn<1, false><<<grid, block, smem, s>>>(t->g, q, N, tile, a, rho0, idx, d2, nullptr);
+        }
+    } else {
+        if (with_cov) {
+            k_knn<2, true><<<grid, block, smem, s>>>(t->g, q, N, tile, a, rho0, idx, d2, cov);
+        } else {
+            k_knn<2, false><<<grid, block, smem, s>>>(t->g, q, N, tile, a, rho0, idx, d2, nullptr);
+        }
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t pc_launch_cov(const pc_target_s* t, const int32_t* idx, int64_t N, int k, float eps,
+                          float* cov, cudaStream_t s) {
+    if (N == 0) return cudaSuccess;
+    const int threads = 128;
+    const int64_t blocks = (N + threads - 1) / threads;
+    k_cov<<<(unsigned)blocks, threads, 0, s>>>(t->g, idx, N, k, eps, cov);
+    return cudaGetLastError();
+}
+
+cudaError_t pc_launch_knn_batch(const pc_target_s* t, const ScanDesc* scans_dev, int nscans,
+                                int64_t total_tiles, int tile, int warps, int blocks, int k,
+                                float eps, bool with_cov, float rho0,
+                                unsigned long long* counter, cudaStream_t s) {
+    TileArgs a{k, eps, t->tune.rho_scale > 0 ? t->tune.rho_scale : 1.15f};
+    const size_t smem = (size_t)warps * warp_smem_bytes(k, with_cov);
+    const dim3 grid((unsigned)blocks), block(warps * 32);
+    if (k <= 32) {
+        if (with_cov) {
+            k_knn_batch<1, true><<<grid, block, smem, s>>>(t->g, scans_dev, nscans, total_tiles,
+                                                         tile, a, rho0, counter);
+        } else {
+            k_knn_batch<1, false><<<grid, block, smem, s>>>(t->g, scans_dev, nscans, total_tiles,
+                                                          tile, a, rho0, counter);
+        }
+    } else {
+        if (with_cov) {
+            k_knn_batch<2, true><<<grid, block, smem, s>>>(t->g, scans_dev, nscans, total_tiles,
+                                                         tile, a, rho0, counter);
+        } else {
+            k_knn_batch<2, false><<<grid, block, smem, s>>>(t->g, scans_dev, nscans, total_tiles,
+                                                          tile, a, rho0, counter);
+        }
+    }
+    return cudaGetLastError();
+}
+
+size_t pc_knn_smem_per_warp(int k, bool with_cov) { return warp_smem_bytes(k, with_cov); }
+
+int pc_knn_batch_blocks(int k, bool with_cov, int warps) {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const size_t smem = (size_t)warps * warp_smem_bytes(k, with_cov);
+    cudaError_t e = ensure_attrs();
+    if (e != cudaSuccess) return sms;
+    if (k <= 32) {
+        if (with_cov) {
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_knn_batch<1, true>, warps * 32, smem);
+        } else {
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_knn_batch<1, false>, warps * 32, smem);
+        }
+    } else {
+        if (with_cov) {
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_knn_batch<2, true>, warps * 32, smem);
+        } else {
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_knn_batch<2, false>, warps * 32, smem);
+        }
+    }
+    if (e != cudaSuccess || per_sm < 1) per_sm = 1;
+    return sms * per_sm;
+}

@@ -1,0 +1,465 @@
+// The C ABI of libpc.so (declared in include/pc.h): argument checks, handle
+// lifetime, search-radius calibration, host-buffer entry, status word and
+// the batched plan with CUDA-graph replay.  No torch types cross it.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <set>
+#include <vector>
+
+#include "pc_internal.h"
+
+namespace {
+
+std::mutex g_mu;
+std::set<const void*> g_live;  // live target and batch handles
+
+bool live(const void* h) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    return g_live.count(h) != 0;
+}
+void track(const void* h) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_live.insert(h);
+}
+void untrack(const void* h) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_live.erase(h);
+}
+
+// Device (or managed) memory reachable by kernels; host, pinned and
+// unregistered pointers are refused.
+bool is_device_ptr(const void* p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+        else prev = -1;
+    }
+    ~DeviceGuard() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+pc_status check_target(const pc_target_s* t) {
+    if (!t) return PC_ERR_INVALID_ARG;
+    if (!live(t)) return PC_ERR_DESTROYED;
+    return PC_OK;
+}
+
+pc_status check_query_args(const pc_target_s* t, int64_t N, int k) {
+    if (k < 1 || k > 64 || N < 0) return PC_ERR_INVALID_ARG;
+    if ((int64_t)k > t->g.m) return PC_ERR_K_GT_M;
+    if (N > ((int64_t)1 << 40)) return PC_ERR_INVALID_ARG;
+    return PC_OK;
+}
+
+void default_tune(pc_tune* tu) {
+    tu->tile = 32;
+    tu->warps = 4;
+    tu->rho_scale = 1.15f;
+}
+
+pc_status read_and_clear_status(pc_target_s* t, cudaStream_t s) {
+    int st = 0;
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&st, t->status, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(t->status, 0, sizeof(int), s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return pc_from_cuda(e);
+    if (st & pcdev::ST_NONFINITE) return PC_ERR_NONFINITE;
+    if (st & pcdev::ST_SEARCH_LIMIT) return PC_ERR_SEARCH_LIMIT;
+    if (st & pcdev::ST_BAD_INDEX) return PC_ERR_BAD_INDEX;
+    return PC_OK;
+}
+
+// First search radius per k: the 75th percentile of the k-th neighbour
+// distance over up to 1024 target points used as queries.  It only sets
+// where the widening search starts; results never depend on it.
+pc_status calibrate_rho(pc_target_s* t, cudaStream_t s) {
+    const int64_t M = t->g.m;
+    const int kc = (int)std::min<int64_t>(64, M);
+    const int64_t S = std::min<int64_t>(M, 1024);
+    const int64_t step = M / S;
+    float* q = nullptr;
+    int32_t* idx = nullptr;
+    float* d2 = nullptr;
+    cudaError_t e = cudaMalloc(&q, sizeof(float) * 3 * S);
+    if (e == cudaSuccess) e = cudaMalloc(&idx, sizeof(int32_t) * S * kc);
+    if (e == cudaSuccess) e = cudaMalloc(&d2, sizeof(float) * S * kc);
+    std::vector<float> hd((size_t)S * kc);
+    if (e == cudaSuccess)
+        e = cudaMemcpy2DAsync(q, 3 * sizeof(float), t->xyz, sizeof(float4) * step, 3 * sizeof(float),
+                              S, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) e = pc_launch_knn(t, q, S, kc, -1.0f, idx, d2, nullptr, t->g.h, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(hd.data(), d2, sizeof(float) * S * kc, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (q) cudaFree(q);
+    if (idx) cudaFree(idx);
+    if (d2) cudaFree(d2);
+    if (e != cudaSuccess) return pc_from_cuda(e);
+    read_and_clear_status(t, s);  // a capped search here only skips that sample
+    std::vector<float> col;
+    for (int kk = 0; kk < 64; ++kk) {
+        t->rho_hint[kk] = 0.0f;
+        if (kk >= kc) continue;
+        col.clear();
+        for (int64_t n = 0; n < S; ++n) {
+            const float v = hd[(size_t)n * kc + kk];
+            if (std::isfinite(v)) col.push_back(std::sqrt(v));
+        }
+        if (col.empty()) continue;
+        const size_t pos = (col.size() * 3) / 4;
+        std::nth_element(col.begin(), col.begin() + pos, col.end());
+        t->rho_hint[kk] = col[pos];
+    }
+    return PC_OK;
+}
+
+pc_status ensure_stage(pc_target_s* t, size_t bytes) {
+    if (t->stage_bytes >= bytes) return PC_OK;
+    if (t->stage) {
+        cudaFree(t->stage);
+        t->stage = nullptr;
+        t->stage_bytes = 0;
+    }
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) return pc_from_cuda(e);
+    t->stage = p;
+    t->stage_bytes = bytes;
+    return PC_OK;
+}
+
+size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+}  // namespace
+
+pc_status pc_from_cuda(cudaError_t e) {
+    if (e == cudaSuccess) return PC_OK;
+    cudaGetLastError();  // clear a non-sticky error
+    if (e == cudaErrorMemoryAllocation) return PC_ERR_OOM;
+    return PC_ERR_CUDA;
+}
+
+float pc_rho0(const pc_target_s* t, int k) {
+    float r = (k >= 1 && k <= 64) ? t->rho_hint[k - 1] : 0.0f;
+    if (!(r > 0.0f)) r = t->g.h;
+    const float sc = t->tune.rho_scale > 0 ? t->tune.rho_scale : 1.15f;
+    return r * sc;
+}
+
+extern "C" {
+
+void pc_default_build_opts(pc_build_opts* o) {
+    if (!o) return;
+    o->cell_size = 0.0f;
+    o->occupancy = 6.0f;
+    o->hash_load = 0.5f;
+    o->max_box_cells = 4096;
+    o->exhaustive = 1;
+}
+
+pc_status pc_build_target(const float* xyz_dev, int64_t M, const pc_build_opts* opts, pc_stream s,
+                          pc_target* out) {
+    if (!out) return PC_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!xyz_dev || M < 1 || M >= ((int64_t)1 << 31)) return PC_ERR_INVALID_ARG;
+    if (!is_device_ptr(xyz_dev)) return PC_ERR_BAD_POINTER;
+    pc_build_opts o;
+    pc_default_build_opts(&o);
+    if (opts) o = *opts;
+    if (o.occupancy <= 0) o.occupancy = 6.0f;
+    if (o.hash_load <= 0 || o.hash_load > 0.9f) o.hash_load = 0.5f;
+    if (o.max_box_cells <= 0) o.max_box_cells = 4096;
+    pc_target_s* t = new (std::nothrow) pc_target_s();
+    if (!t) return PC_ERR_OOM;
+    std::memset(t, 0, sizeof(*t));
+    t->magic = PC_MAGIC_LIVE;
+    cudaGetDevice(&t->device);
+    t->opts = o;
+    default_tune(&t->tune);
+    cudaStream_t st = (cudaStream_t)s;
+    pc_status r = pc_build_grid(xyz_dev, M, o, st, t);
+    if (r == PC_OK) r = calibrate_rho(t, st);
+    if (r != PC_OK) {
+        cudaStreamSynchronize(st);
+        pc_free_grid(t);
+        delete t;
+        return r;
+    }
+    track(t);
+    *out = t;
+    return PC_OK;
+}
+
+void pc_destroy_target(pc_target t) {
+    if (!t || !live(t)) return;
+    untrack(t);
+    DeviceGuard dg(t->device);
+    pc_free_grid(t);
+    t->magic = PC_MAGIC_DEAD;
+    delete t;
+}
+
+pc_status pc_set_tune(pc_target t, const pc_tune* tune) {
+    pc_status r = check_target(t);
+    if (r != PC_OK) return r;
+    if (!tune) {
+        default_tune(&t->tune);
+        return PC_OK;
+    }
+    if (tune->tile > 32 || tune->warps > 16 || !(std::isfinite(tune->rho_scale)))
+        return PC_ERR_INVALID_ARG;
+    t->tune = *tune;
+    if (t->tune.tile <= 0) t->tune.tile = 32;
+    if (t->tune.warps <= 0) t->tune.warps = 4;
+    if (t->tune.rho_scale <= 0) t->tune.rho_scale = 1.15f;
+    return PC_OK;
+}
+
+pc_status pc_get_info(pc_target t, pc_target_info* info) {
+    pc_status r = check_target(t);
+    if (r != PC_OK) return r;
+    if (!info) return PC_ERR_INVALID_ARG;
+    info->m = t->g.m;
+    info->ncells = t->g.ncells;
+    info->table_cap = t->table_cap;
+    info->cell_size = t->g.h;
+    info->origin[0] = t->g.ox;
+    info->origin[1] = t->g.oy;
+    info->origin[2] = t->g.oz;
+    for (int a = 0; a < 3; ++a) info->bbox_max[a] = t->bbox_max[a];
+    info->dims[0] = t->g.dimx;
+    info->dims[1] = t->g.dimy;
+    info->dims[2] = t->g.dimz;
+    info->device_bytes = t->device_bytes + (int64_t)t->stage_bytes;
+    for (int i = 0; i < 64; ++i) info->rho_hint[i] = t->rho_hint[i];
+    return PC_OK;
+}
+
+pc_status pc_knn(pc_target t, const float* q_dev, int64_t N, int k, int32_t* idx_dev,
+                 float* d2_dev, pc_stream s) {
+    pc_status r = check_target(t);
+    if (r != PC_OK) return r;
+    if ((r = check_query_args(t, N, k)) != PC_OK) return r;
+    if (N == 0) return PC_OK;
+    if (!q_dev || !idx_dev || !d2_dev) return PC_ERR_INVALID_ARG;
+    if (!is_device_ptr(q_dev) || !is_device_ptr(idx_dev) || !is_device_ptr(d2_dev))
+        return PC_ERR_BAD_POINTER;
+    DeviceGuard dg(t->device);
+    return pc_from_cuda(
+        pc_launch_knn(t, q_dev, N, k, -1.0f, idx_dev, d2_dev, nullptr, pc_rho0(t, k), (cudaStream_t)s));
+}
+
+pc_status pc_cov(pc_target t, const int32_t* idx_dev, int64_t N, int k, float eps, float* cov_dev,
+                 pc_stream s) {
+    pc_status r = check_target(t);
+    if (r != PC_OK) return r;
+    if (k < 1 || k > 64 || N < 0 || !std::isfinite(eps)) return PC_ERR_INVALID_ARG;
+    if (N == 0) return PC_OK;
+    if (!idx_dev || !cov_dev) return PC_ERR_INVALID_ARG;
+    if (!is_device_ptr(idx_dev) || !is_device_ptr(cov_dev)) return PC_ERR_BAD_POINTER;
+    DeviceGuard dg(t->device);
+    return pc_from_cuda(pc_launch_cov(t, idx_dev, N, k, eps, cov_dev, (cudaStream_t)s));
+}
+
+pc_status pc_knn_cov(pc_target t, const float* q_dev, int64_t N, int k, float eps,
+                     int32_t* idx_dev, float* d2_dev, float* cov_dev, pc_stream s) {
+    pc_status r = check_target(t);
+    if (r != PC_OK) return r;
+    if ((r = check_query_args(t, N, k)) != PC_OK) return r;
+    if (!std::isfinite(eps)) return PC_ERR_INVALID_ARG;
+    if (N == 0) return PC_OK;
+    if (!q_dev || !idx_dev || !d2_dev || !cov_dev) return PC_ERR_INVALID_ARG;
+    if (!is_device_ptr(q_dev) || !is_device_ptr(idx_dev) || !is_device_ptr(d2_dev) ||
+        !is_device_ptr(cov_dev))
+        return PC_ERR_BAD_POINTER;
+    DeviceGuard dg(t->device);
+    return pc_from_cuda(pc_launch_knn(t, q_dev, N, k, eps, idx_dev, d2_dev, cov_dev, pc_rho0(t, k),
+                                      (cudaStream_t)s));
+}
+
+pc_status pc_knn_cov_host(pc_target t, const float* q_host, int64_t N, int k, float eps,
+                          int32_t* idx_host, float* d2_host, float* cov_host, pc_stream s) {
+    pc_status r = check_target(t);
+    if (r != PC_OK) return r;
+    if ((r = check_query_args(t, N, k)) != PC_OK) return r;
+    if (!std::isfinite(eps)) return PC_ERR_INVALID_ARG;
+    if (N == 0) return PC_OK;
+    if (!q_host || !idx_host || !d2_host || !cov_host) return PC_ERR_INVALID_ARG;
+    DeviceGuard dg(t->device);
+    const size_t bq = align256(sizeof(float) * 3 * N), bi = align256(sizeof(int32_t) * N * k),
+                 bd = align256(sizeof(float) * N * k), bc = align256(sizeof(float) * 6 * N);
+    if ((r = ensure_stage(t, bq + bi + bd + bc)) != PC_OK) return r;
+    char* base = static_cast<char*>(t->stage);
+    float* q = reinterpret_cast<float*>(base);
+    int32_t* idx = reinterpret_cast<int32_t*>(base + bq);
+    float* d2 = reinterpret_cast<float*>(base + bq + bi);
+    float* cov = reinterpret_cast<float*>(base + bq + bi + bd);
+    cudaStream_t st = (cudaStream_t)s;
+    cudaError_t e = cudaMemcpyAsync(q, q_host, sizeof(float) * 3 * N, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = pc_launch_knn(t, q, N, k, eps, idx, d2, cov, pc_rho0(t, k), st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(idx_host, idx, sizeof(int32_t) * N * k, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(d2_host, d2, sizeof(float) * N * k, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(cov_host, cov, sizeof(float) * 6 * N, cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) return pc_from_cuda(e);
+    return read_and_clear_status(t, st);
+}
+
+pc_status pc_sync_status(pc_target t, pc_stream s) {
+    pc_status r = check_target(t);
+    if (r != PC_OK) return r;
+    DeviceGuard dg(t->device);
+    return read_and_clear_status(t, (cudaStream_t)s);
+}
+
+pc_status pc_batch_plan(pc_target t, const pc_scan* scans, int n_scans, int k, float eps,
+                        pc_batch* out) {
+    if (!out) return PC_ERR_INVALID_ARG;
+    *out = nullptr;
+    pc_status r = check_target(t);
+    if (r != PC_OK) return r;
+    if (!scans || n_scans < 1 || k < 1 || k > 64 || !std::isfinite(eps)) return PC_ERR_INVALID_ARG;
+    if ((int64_t)k > t->g.m) return PC_ERR_K_GT_M;
+    bool any_cov = false;
+    for (int i = 0; i < n_scans; ++i) {
+        const pc_scan& sc = scans[i];
+        if (sc.n < 0) return PC_ERR_INVALID_ARG;
+        if (sc.n == 0) continue;
+        if (!sc.q_dev || !sc.idx_dev || !sc.d2_dev) return PC_ERR_INVALID_ARG;
+        if (!is_device_ptr(sc.q_dev) || !is_device_ptr(sc.idx_dev) || !is_device_ptr(sc.d2_dev))
+            return PC_ERR_BAD_POINTER;
+        if (sc.cov_dev) {
+            if (!is_device_ptr(sc.cov_dev)) return PC_ERR_BAD_POINTER;
+            any_cov = true;
+        }
+    }
+    DeviceGuard dg(t->device);
+    pc_batch_s* b = new (std::nothrow) pc_batch_s();
+    if (!b) return PC_ERR_OOM;
+    std::memset(b, 0, sizeof(*b));
+    b->magic = PC_MAGIC_LIVE;
+    b->t = t;
+    b->n_scans = n_scans;
+    b->k = k;
+    b->eps = eps;
+    b->with_cov = any_cov;
+    b->tile = std::min(std::max(t->tune.tile, 1), 32);
+    b->warps = std::min(std::max(t->tune.warps, 1), 16);
+    std::vector<ScanDesc> hs(n_scans);
+    int64_t tiles = 0, queries = 0;
+    for (int i = 0; i < n_scans; ++i) {
+        hs[i].q = scans[i].q_dev;
+        hs[i].n = scans[i].n;
+        hs[i].idx = scans[i].idx_dev;
+        hs[i].d2 = scans[i].d2_dev;
+        hs[i].cov = scans[i].cov_dev;
+        hs[i].tile0 = tiles;
+        tiles += (scans[i].n + b->tile - 1) / b->tile;
+        queries += scans[i].n;
+    }
+    b->total_tiles = tiles;
+    b->total_queries = queries;
+    b->blocks = pc_knn_batch_blocks(k, any_cov, b->warps);
+    cudaError_t e = cudaMalloc(&b->scans_dev, sizeof(ScanDesc) * n_scans);
+    if (e == cudaSuccess) e = cudaMalloc(&b->counter, sizeof(unsigned long long));
+    if (e == cudaSuccess)
+        e = cudaMemcpy(b->scans_dev, hs.data(), sizeof(ScanDesc) * n_scans, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        if (b->scans_dev) cudaFree(b->scans_dev);
+        if (b->counter) cudaFree(b->counter);
+        delete b;
+        return pc_from_cuda(e);
+    }
+    track(b);
+    *out = b;
+    return PC_OK;
+}
+
+pc_status pc_batch_run(pc_batch b, pc_stream s) {
+    if (!b) return PC_ERR_INVALID_ARG;
+    if (!live(b)) return PC_ERR_DESTROYED;
+    if (!live(b->t)) return PC_ERR_DESTROYED;
+    if (b->total_tiles == 0) return PC_OK;
+    DeviceGuard dg(b->t->device);
+    cudaStream_t st = (cudaStream_t)s;
+    const float rho0 = pc_rho0(b->t, b->k);
+    if (st == nullptr) {  // the legacy stream cannot be captured: launch directly
+        cudaError_t e = cudaMemsetAsync(b->counter, 0, sizeof(unsigned long long), st);
+        if (e == cudaSuccess)
+            e = pc_launch_knn_batch(b->t, b->scans_dev, b->n_scans, b->total_tiles, b->tile,
+                                    b->warps, b->blocks, b->k, b->eps, b->with_cov, rho0,
+                                    b->counter, st);
+        return pc_from_cuda(e);
+    }
+    if (!b->exec || b->captured_on != st) {
+        if (b->exec) cudaGraphExecDestroy(b->exec);
+        if (b->graph) cudaGraphDestroy(b->graph);
+        b->exec = nullptr;
+        b->graph = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return pc_from_cuda(e);
+        cudaError_t e1 = cudaMemsetAsync(b->counter, 0, sizeof(unsigned long long), st);
+        cudaError_t e2 = pc_launch_knn_batch(b->t, b->scans_dev, b->n_scans, b->total_tiles,
+                                             b->tile, b->warps, b->blocks, b->k, b->eps,
+                                             b->with_cov, rho0, b->counter, st);
+        e = cudaStreamEndCapture(st, &b->graph);
+        if (e1 != cudaSuccess) e = e1;
+        if (e2 != cudaSuccess) e = e2;
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+        if (e != cudaSuccess) {
+            if (b->graph) cudaGraphDestroy(b->graph);
+            b->graph = nullptr;
+            b->exec = nullptr;
+            return pc_from_cuda(e);
+        }
+        b->captured_on = st;
+    }
+    return pc_from_cuda(cudaGraphLaunch(b->exec, st));
+}
+
+void pc_batch_destroy(pc_batch b) {
+    if (!b || !live(b)) return;
+    untrack(b);
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    if (b->scans_dev) cudaFree(b->scans_dev);
+    if (b->counter) cudaFree(b->counter);
+    b->magic = PC_MAGIC_DEAD;
+    delete b;
+}
+
+const char* pc_status_string(pc_status st) {
+    switch (st) {
+        case PC_OK: return "ok";
+        case PC_ERR_INVALID_ARG: return "invalid argument";
+        case PC_ERR_K_GT_M: return "k larger than the target size";
+        case PC_ERR_NONFINITE: return "non-finite coordinate";
+        case PC_ERR_OOM: return "device allocation failed";
+        case PC_ERR_CUDA: return "CUDA runtime error";
+        case PC_ERR_SEARCH_LIMIT: return "search reached max_box_cells (exhaustive scan disabled)";
+        case PC_ERR_BAD_POINTER: return "pointer is not device memory";
+        case PC_ERR_BAD_INDEX: return "neighbour index outside the target";
+        case PC_ERR_DESTROYED: return "handle destroyed or never built";
+    }
+    return "unknown status";
+}
+
+const char* pc_version(void) { return "pc 0.1 sm_103a"; }
+
+}  // extern "C"

@@ -1,0 +1,86 @@
+// Device-side definitions shared by the grid build and the search kernels:
+// the voxel-hash grid layout, the cell-coordinate rule and the hash probe.
+//
+// The grid is the "GPU-hash data structure" over the target of Sec. III-C3:
+// every target point p lands in the cell
+//     c_a = floor( fl( fl(p_a - o_a) * inv_h ) ),  a in {x, y, z}
+// (o = bounding-box minimum, inv_h = fl(1/h)); queries use the same rule, so
+// the rounding error of the rule is the same on both sides and the search
+// can bound it (see certified_radius2 in knn_cov.cu).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace pcdev {
+
+constexpr unsigned FULL = 0xffffffffu;
+constexpr unsigned long long EMPTY_KEY = ~0ull;
+
+// status-word bits (one int per target handle)
+constexpr int ST_NONFINITE = 1;
+constexpr int ST_SEARCH_LIMIT = 2;
+constexpr int ST_BAD_INDEX = 4;
+
+// Read-only view of a built target, passed by value to every search kernel.
+struct Grid {
+    float ox, oy, oz;       // origin = bbox minimum
+    float h, inv_h;         // cell edge and fl(1/h)
+    int dimx, dimy, dimz;   // occupied range of cell coordinates is [0, dim)
+    int bx, by;             // key = cx | cy << bx | cz << (bx + by)
+    int log2cap;            // hash capacity = 1 << log2cap
+    int max_box_cells;
+    int exhaustive;
+    float coord_scale;      // max |coordinate| over origin and bbox corners
+    int64_t m;              // target points
+    int64_t ncells;         // occupied cells
+    const uint4* table;     // slot = {key lo, key hi, start, count}
+    const float4* pts;      // cell-sorted: (x, y, z, bits of the original index)
+    const float4* xyz;      // caller order: (x, y, z, 0)
+    const unsigned long long* cell_keys;  // occupied cell keys, ascending [ncells]
+    const uint32_t* cell_start;           // [ncells + 1] into pts
+    int* status;
+};
+
+__device__ __forceinline__ int cell_of(float v, float o, float inv_h) {
+    float t = __fmul_rn(__fsub_rn(v, o), inv_h);
+    t = floorf(t);
+    t = fminf(fmaxf(t, -1073741824.0f), 1073741824.0f);
+    return (int)t;
+}
+
+__device__ __forceinline__ unsigned long long pack_key(int cx, int cy, int cz, int bx, int by) {
+    return (unsigned long long)(unsigned)cx | ((unsigned long long)(unsigned)cy << bx) |
+           ((unsigned long long)(unsigned)cz << (bx + by));
+}
+
+__device__ __forceinline__ uint32_t hash_slot(unsigned long long key, int log2cap) {
+    return (uint32_t)((key * 0x9E3779B97F4A7C15ull) >> (64 - log2cap));
+}
+
+// (start, count) of an occupied cell, (0, 0) for an empty one.  Linear
+// probing; the table always has empty slots (load <= 0.9), and the probe
+// count is capped at the capacity anyway.
+__device__ __forceinline__ uint2 lookup_cell(const Grid& g, unsigned long long key) {
+    const uint32_t mask = (1u << g.log2cap) - 1u;
+    uint32_t slot = hash_slot(key, g.log2cap);
+    for (uint32_t probe = 0; probe <= mask; ++probe) {
+        uint4 e = __ldg(&g.table[slot]);
+        unsigned long long k = (unsigned long long)e.x | ((unsigned long long)e.y << 32);
+        if (k == key) return make_uint2(e.z, e.w);
+        if (k == EMPTY_KEY) break;
+        slot = (slot + 1u) & mask;
+    }
+    return make_uint2(0u, 0u);
+}
+
+// The pinned binary32 squared distance: fmaf(dz,dz, fmaf(dy,dy, dx*dx)).
+__device__ __forceinline__ float sqdist_pinned(float qx, float qy, float qz, float px, float py,
+                                               float pz) {
+    float dx = __fsub_rn(qx, px);
+    float dy = __fsub_rn(qy, py);
+    float dz = __fsub_rn(qz, pz);
+    return __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
+}
+
+}  // namespace pcdev

@@ -1,0 +1,84 @@
+// Host-side definitions shared by the library's translation units.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "pc.h"
+#include "pc_device.cuh"
+
+constexpr uint32_t PC_MAGIC_LIVE = 0x70637467u;  // "pctg"
+constexpr uint32_t PC_MAGIC_DEAD = 0xdeadbeefu;
+
+// One scan of a batched launch, as the persistent kernel sees it.
+struct ScanDesc {
+    const float* q;
+    int64_t n;
+    int32_t* idx;
+    float* d2;
+    float* cov;     // may be null: no covariance for this scan
+    int64_t tile0;  // first work item of this scan
+};
+
+struct pc_target_s {
+    uint32_t magic;
+    int device;
+    pcdev::Grid g;        // kernel view; the pointers below back it
+    pc_build_opts opts;
+    pc_tune tune;
+    float bbox_max[3];
+    float rho_hint[64];
+    int64_t table_cap;
+    int64_t device_bytes;
+    // owned device memory
+    uint4* table;
+    float4* pts;
+    float4* xyz;
+    unsigned long long* cell_keys;
+    uint32_t* cell_start;
+    int* status;
+    // staging for pc_knn_cov_host, grown on demand
+    void* stage;
+    size_t stage_bytes;
+};
+
+struct pc_batch_s {
+    uint32_t magic;
+    pc_target_s* t;
+    int n_scans;
+    int k;
+    float eps;
+    bool with_cov;
+    int tile;
+    int warps;
+    int blocks;
+    int64_t total_tiles;
+    int64_t total_queries;
+    ScanDesc* scans_dev;
+    unsigned long long* counter;
+    cudaGraph_t graph;
+    cudaGraphExec_t exec;
+    cudaStream_t captured_on;
+};
+
+// grid_build.cu
+pc_status pc_build_grid(const float* xyz, int64_t M, const pc_build_opts& o, cudaStream_t s,
+                        pc_target_s* t);
+void pc_free_grid(pc_target_s* t);
+
+// knn_cov.cu
+cudaError_t pc_launch_knn(const pc_target_s* t, const float* q, int64_t N, int k, float eps,
+                          int32_t* idx, float* d2, float* cov, float rho0, cudaStream_t s);
+cudaError_t pc_launch_cov(const pc_target_s* t, const int32_t* idx, int64_t N, int k, float eps,
+                          float* cov, cudaStream_t s);
+cudaError_t pc_launch_knn_batch(const pc_target_s* t, const ScanDesc* scans_dev, int nscans,
+                                int64_t total_tiles, int tile, int warps, int blocks, int k,
+                                float eps, bool with_cov, float rho0,
+                                unsigned long long* counter, cudaStream_t s);
+size_t pc_knn_smem_per_warp(int k, bool with_cov);
+int pc_knn_batch_blocks(int k, bool with_cov, int warps);
+
+// pc_api.cu
+float pc_rho0(const pc_target_s* t, int k);
+pc_status pc_from_cuda(cudaError_t e);

@@ -1,0 +1,380 @@
+"""Thin ctypes binding of libpc.so (include/pc.h).
+
+The module-level ``pc_*`` functions mirror the C ABI one to one (argument
+marshalling only: pointers, sizes, streams).  ``Target`` and ``Batch`` wrap
+them for torch CUDA tensors.  PyTorch only provides device memory and
+streams; every step of the computation runs in the library's kernels.
+
+There is no fallback: if libpc.so cannot be loaded, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libpc.so")
+
+PC_OK = 0
+PC_ERR_INVALID_ARG = 1
+PC_ERR_K_GT_M = 2
+PC_ERR_NONFINITE = 3
+PC_ERR_OOM = 4
+PC_ERR_CUDA = 5
+PC_ERR_SEARCH_LIMIT = 6
+PC_ERR_BAD_POINTER = 7
+PC_ERR_BAD_INDEX = 8
+PC_ERR_DESTROYED = 9
+
+_STATUS_NAMES = {
+    0: "PC_OK",
+    1: "PC_ERR_INVALID_ARG",
+    2: "PC_ERR_K_GT_M",
+    3: "PC_ERR_NONFINITE",
+    4: "PC_ERR_OOM",
+    5: "PC_ERR_CUDA",
+    6: "PC_ERR_SEARCH_LIMIT",
+    7: "PC_ERR_BAD_POINTER",
+    8: "PC_ERR_BAD_INDEX",
+    9: "PC_ERR_DESTROYED",
+}
+
+
+class PcError(RuntimeError):
+    def __init__(self, code: int, where: str = ""):
+        self.code = int(code)
+        msg = _STATUS_NAMES.get(self.code, str(code))
+        try:
+            msg += ": " + _lib.pc_status_string(self.code).decode()
+        except Exception:
+            pass
+        super().__init__(f"{where}: {msg}" if where else msg)
+
+
+class pc_build_opts(ctypes.Structure):
+    _fields_ = [
+        ("cell_size", ctypes.c_float),
+        ("occupancy", ctypes.c_float),
+        ("hash_load", ctypes.c_float),
+        ("max_box_cells", ctypes.c_int),
+        ("exhaustive", ctypes.c_int),
+    ]
+
+
+class pc_tune(ctypes.Structure):
+    _fields_ = [("tile", ctypes.c_int), ("warps", ctypes.c_int), ("rho_scale", ctypes.c_float)]
+
+
+class pc_target_info(ctypes.Structure):
+    _fields_ = [
+        ("m", ctypes.c_int64),
+        ("ncells", ctypes.c_int64),
+        ("table_cap", ctypes.c_int64),
+        ("cell_size", ctypes.c_float),
+        ("origin", ctypes.c_float * 3),
+        ("bbox_max", ctypes.c_float * 3),
+        ("dims", ctypes.c_int * 3),
+        ("device_bytes", ctypes.c_int64),
+        ("rho_hint", ctypes.c_float * 64),
+    ]
+
+
+class pc_scan(ctypes.Structure):
+    _fields_ = [
+        ("q_dev", ctypes.c_void_p),
+        ("n", ctypes.c_int64),
+        ("idx_dev", ctypes.c_void_p),
+        ("d2_dev", ctypes.c_void_p),
+        ("cov_dev", ctypes.c_void_p),
+    ]
+
+
+# (name, restype, argtypes): the C ABI of include/pc.h
+_VP, _I64, _INT, _F = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_float
+SIGNATURES = {
+    "pc_default_build_opts": (None, [ctypes.POINTER(pc_build_opts)]),
+    "pc_build_target": (_INT, [_VP, _I64, ctypes.POINTER(pc_build_opts), _VP, ctypes.POINTER(_VP)]),
+    "pc_destroy_target": (None, [_VP]),
+    "pc_set_tune": (_INT, [_VP, ctypes.POINTER(pc_tune)]),
+    "pc_get_info": (_INT, [_VP, ctypes.POINTER(pc_target_info)]),
+    "pc_knn": (_INT, [_VP, _VP, _I64, _INT, _VP, _VP, _VP]),
+    "pc_cov": (_INT, [_VP, _VP, _I64, _INT, _F, _VP, _VP]),
+    "pc_knn_cov": (_INT, [_VP, _VP, _I64, _INT, _F, _VP, _VP, _VP, _VP]),
+    "pc_knn_cov_host": (_INT, [_VP, _VP, _I64, _INT, _F, _VP, _VP, _VP, _VP]),
+    "pc_sync_status": (_INT, [_VP, _VP]),
+    "pc_batch_plan": (_INT, [_VP, ctypes.POINTER(pc_scan), _INT, _INT, _F, ctypes.POINTER(_VP)]),
+    "pc_batch_run": (_INT, [_VP, _VP]),
+    "pc_batch_destroy": (None, [_VP]),
+    "pc_status_string": (ctypes.c_char_p, [_INT]),
+    "pc_version": (ctypes.c_char_p, []),
+}
+
+_lib = None
+
+
+def load(path: Optional[str] = None, build_if_missing: bool = True):
+    """Load libpc.so (building it in-tree with nvcc if it is missing)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIB_PATH
+    if not os.path.exists(path):
+        if not build_if_missing:
+            raise OSError(f"libpc.so not built at {path}")
+        from . import _build
+
+        _build.build()
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(rc: int, where: str):
+    if rc != PC_OK:
+        raise PcError(rc, where)
+
+
+# ---------------------------------------------------------------- raw ABI
+def pc_default_build_opts() -> pc_build_opts:
+    o = pc_build_opts()
+    load().pc_default_build_opts(ctypes.byref(o))
+    return o
+
+
+def pc_build_target(xyz_dev: int, M: int, opts: Optional[pc_build_opts], stream: int) -> int:
+    h = ctypes.c_void_p()
+    rc = load().pc_build_target(xyz_dev, M, ctypes.byref(opts) if opts is not None else None, stream, ctypes.byref(h))
+    _check(rc, "pc_build_target")
+    return h.value
+
+
+def pc_destroy_target(t: int) -> None:
+    load().pc_destroy_target(t)
+
+
+def pc_set_tune(t: int, tune: Optional[pc_tune]) -> None:
+    _check(load().pc_set_tune(t, ctypes.byref(tune) if tune is not None else None), "pc_set_tune")
+
+
+def pc_get_info(t: int) -> pc_target_info:
+    info = pc_target_info()
+    _check(load().pc_get_info(t, ctypes.byref(info)), "pc_get_info")
+    return info
+
+
+def pc_knn(t, q_dev, N, k, idx_dev, d2_dev, stream) -> int:
+    return load().pc_knn(t, q_dev, N, k, idx_dev, d2_dev, stream)
+
+
+def pc_cov(t, idx_dev, N, k, eps, cov_dev, stream) -> int:
+    return load().pc_cov(t, idx_dev, N, k, eps, cov_dev, stream)
+
+
+def pc_knn_cov(t, q_dev, N, k, eps, idx_dev, d2_dev, cov_dev, stream) -> int:
+    return load().pc_knn_cov(t, q_dev, N, k, eps, idx_dev, d2_dev, cov_dev, stream)
+
+
+def pc_knn_cov_host(t, q_host, N, k, eps, idx_host, d2_host, cov_host, stream) -> int:
+    return load().pc_knn_cov_host(t, q_host, N, k, eps, idx_host, d2_host, cov_host, stream)
+
+
+def pc_sync_status(t, stream) -> int:
+    return load().pc_sync_status(t, stream)
+
+
+def pc_batch_plan(t, scans: Sequence[pc_scan], k: int, eps: float) -> int:
+    arr = (pc_scan * len(scans))(*scans)
+    h = ctypes.c_void_p()
+    _check(load().pc_batch_plan(t, arr, len(scans), k, eps, ctypes.byref(h)), "pc_batch_plan")
+    return h.value
+
+
+def pc_batch_run(b, stream) -> int:
+    return load().pc_batch_run(b, stream)
+
+
+def pc_batch_destroy(b) -> None:
+    load().pc_batch_destroy(b)
+
+
+def pc_status_string(code: int) -> str:
+    return load().pc_status_string(code).decode()
+
+
+def pc_version() -> str:
+    return load().pc_version().decode()
+
+
+# ---------------------------------------------------------------- torch layer
+def _torch():
+    import torch
+
+    return torch
+
+
+def _stream_handle(stream=None) -> int:
+    torch = _torch()
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream)
+
+
+def _dev_tensor(x, dtype, shape_tail, name):
+    torch = _torch()
+    if not isinstance(x, torch.Tensor) or not x.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if x.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}")
+    if not x.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if shape_tail is not None and (x.dim() != 2 or x.shape[1] != shape_tail):
+        raise ValueError(f"{name} must be [n,{shape_tail}]")
+    return x
+
+
+class Target:
+    """A device-resident target (map) grid: kNN + covariance queries."""
+
+    def __init__(self, xyz, cell_size: float = 0.0, occupancy: float = 0.0, hash_load: float = 0.0,
+                 max_box_cells: int = 0, exhaustive: bool = True, stream=None):
+        torch = _torch()
+        xyz = _dev_tensor(xyz, torch.float32, 3, "xyz")
+        o = pc_default_build_opts()
+        if cell_size > 0:
+            o.cell_size = cell_size
+        if occupancy > 0:
+            o.occupancy = occupancy
+        if hash_load > 0:
+            o.hash_load = hash_load
+        if max_box_cells > 0:
+            o.max_box_cells = max_box_cells
+        o.exhaustive = 1 if exhaustive else 0
+        self.device = xyz.device
+        self.m = xyz.shape[0]
+        self._h = None
+        self._h = pc_build_target(xyz.data_ptr(), self.m, o, _stream_handle(stream))
+
+    @property
+    def handle(self) -> int:
+        if self._h is None:
+            raise PcError(PC_ERR_DESTROYED, "Target")
+        return self._h
+
+    def info(self) -> dict:
+        i = pc_get_info(self.handle)
+        return {
+            "m": i.m,
+            "ncells": i.ncells,
+            "table_cap": i.table_cap,
+            "cell_size": i.cell_size,
+            "origin": list(i.origin),
+            "bbox_max": list(i.bbox_max),
+            "dims": list(i.dims),
+            "device_bytes": i.device_bytes,
+            "rho_hint": list(i.rho_hint),
+        }
+
+    def set_tune(self, tile: int = 0, warps: int = 0, rho_scale: float = 0.0):
+        pc_set_tune(self.handle, pc_tune(tile, warps, rho_scale))
+
+    def knn(self, q, k: int, idx=None, d2=None, stream=None):
+        torch = _torch()
+        q = _dev_tensor(q, torch.float32, 3, "q")
+        n = q.shape[0]
+        idx = idx if idx is not None else torch.empty((n, k), dtype=torch.int32, device=q.device)
+        d2 = d2 if d2 is not None else torch.empty((n, k), dtype=torch.float32, device=q.device)
+        _check(pc_knn(self.handle, q.data_ptr(), n, k, idx.data_ptr(), d2.data_ptr(), _stream_handle(stream)), "pc_knn")
+        return idx, d2
+
+    def cov(self, idx, eps: float, cov=None, stream=None):
+        torch = _torch()
+        idx = _dev_tensor(idx, torch.int32, None, "idx")
+        n, k = idx.shape
+        cov = cov if cov is not None else torch.empty((n, 6), dtype=torch.float32, device=idx.device)
+        _check(pc_cov(self.handle, idx.data_ptr(), n, k, float(eps), cov.data_ptr(), _stream_handle(stream)), "pc_cov")
+        return cov
+
+    def knn_cov(self, q, k: int, eps: float, idx=None, d2=None, cov=None, stream=None):
+        torch = _torch()
+        q = _dev_tensor(q, torch.float32, 3, "q")
+        n = q.shape[0]
+        dev = q.device
+        idx = idx if idx is not None else torch.empty((n, k), dtype=torch.int32, device=dev)
+        d2 = d2 if d2 is not None else torch.empty((n, k), dtype=torch.float32, device=dev)
+        cov = cov if cov is not None else torch.empty((n, 6), dtype=torch.float32, device=dev)
+        rc = pc_knn_cov(self.handle, q.data_ptr(), n, k, float(eps), idx.data_ptr(), d2.data_ptr(),
+                        cov.data_ptr(), _stream_handle(stream))
+        _check(rc, "pc_knn_cov")
+        return idx, d2, cov
+
+    def knn_cov_host(self, q: np.ndarray, k: int, eps: float, out=None, stream=None):
+        """Host buffers in and out (pinned torch CPU tensors or numpy arrays)."""
+        torch = _torch()
+        if isinstance(q, torch.Tensor):
+            assert q.device.type == "cpu" and q.dtype == torch.float32 and q.is_contiguous()
+            n = q.shape[0]
+            qp = q.data_ptr()
+            if out is None:
+                out = (torch.empty((n, k), dtype=torch.int32), torch.empty((n, k), dtype=torch.float32),
+                       torch.empty((n, 6), dtype=torch.float32))
+            ptrs = [o.data_ptr() for o in out]
+        else:
+            q = np.ascontiguousarray(q, dtype=np.float32)
+            n = q.shape[0]
+            qp = q.ctypes.data
+            if out is None:
+                out = (np.empty((n, k), np.int32), np.empty((n, k), np.float32), np.empty((n, 6), np.float32))
+            ptrs = [o.ctypes.data for o in out]
+        rc = pc_knn_cov_host(self.handle, qp, n, k, float(eps), ptrs[0], ptrs[1], ptrs[2], _stream_handle(stream))
+        _check(rc, "pc_knn_cov_host")
+        return out
+
+    def sync_status(self, stream=None) -> int:
+        return pc_sync_status(self.handle, _stream_handle(stream))
+
+    def close(self):
+        if self._h is not None:
+            pc_destroy_target(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Many scans, one persistent launch replayed as a CUDA graph."""
+
+    def __init__(self, target: Target, scans, k: int, eps: float):
+        """scans: list of (q [n,3] f32, idx [n,k] i32, d2 [n,k] f32, cov [n,6] f32 or None)."""
+        self.target = target
+        self._keep = list(scans)
+        descs = []
+        for q, idx, d2, cov in scans:
+            descs.append(pc_scan(q.data_ptr(), q.shape[0], idx.data_ptr(), d2.data_ptr(),
+                                 cov.data_ptr() if cov is not None else None))
+        self._h = None
+        self._h = pc_batch_plan(target.handle, descs, k, eps)
+
+    def run(self, stream=None):
+        _check(pc_batch_run(self._h, _stream_handle(stream)), "pc_batch_run")
+
+    def close(self):
+        if self._h is not None:
+            pc_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
