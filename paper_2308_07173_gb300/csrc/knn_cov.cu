@@ -28,8 +28,8 @@
 //  5. Epilogue (fused form).  Once the tile is done, lane i computes query
 //     i's covariance from the neighbour indices staged in shared memory:
 //     a two-pass binary32 mean/centred sum shifted by the nearest
-//     neighbour, then -- for eps >= 0 -- the closed-form symmetric 3x3
-//     eigen-solve and C' = I - (1-eps) n n^T.
+//     neighbour, then -- for eps >= 0 -- a binary32 Jacobi eigen-solve
+//     for the normal n and C' = I - (1-eps) n n^T.
 //
 // Everything is exact/deterministic by construction: the tile, the launch
 // shape, rho and the batching never change a result bit.
@@ -324,23 +324,43 @@ __device__ bool knn_search(const Grid& g, float qx, float qy, float qz, int k, f
 }
 
 // ---------------------------------------------------------------- covariance
-__device__ __forceinline__ float3 cross3(float3 a, float3 b) {
-    return make_float3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
-}
-__device__ __forceinline__ float dot3(float3 a, float3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
 
-// Unit eigenvector of the smallest eigenvalue of a symmetric 3x3 matrix.
-// Eigenvalues by the trigonometric closed form for symmetric 3x3 matrices
-// (O. K. Smith, CACM 4(4), 1961): with q = tr/3, p^2 = ||A - qI||_F^2 / 6 and
-// r = det((A - qI)/p)/2, lambda = q + 2p cos(acos(r)/3 + 2 pi j/3); j = 1 is
-// the smallest.  The eigenvector is the largest cross product of two rows of
-// A - lambda_min I (the stable choice discussed by J. Kopp, "Efficient
-// numerical diagonalization of hermitian 3x3 matrices", 2008); when those
-// rows have rank <= 1 (lambda_min repeated) any unit vector orthogonal to
-// the largest row is an eigenvector; a zero or isotropic matrix gives e_z.
-// The matrix is first scaled by an exact power of two so its largest entry
-// lies in [0.5, 1).
-__device__ float3 min_eigvec(float a00, float a01, float a02, float a11, float a12, float a22) {
+// One Jacobi rotation in the (p,q) plane that zeroes a_pq of a symmetric
+// matrix (r is the remaining index): with theta = (a_qq - a_pp) / (2 a_pq)
+// and t the smaller root of t^2 + 2 t theta - 1 = 0, c = 1/sqrt(1+t^2),
+// s = t c, the diagonal moves by -+ t a_pq and the r-row and the
+// eigenvector columns p, q rotate by (c, s) (Golub & Van Loan, sec. 8.5).
+__host__ __device__ __forceinline__ void jacobi_rotate(float& app, float& aqq, float& apq, float& arp,
+                                              float& arq, float& v0p, float& v0q, float& v1p,
+                                              float& v1q, float& v2p, float& v2q) {
+    if (apq == 0.0f) return;
+    const float theta = (aqq - app) / (2.0f * apq);
+    const float at = fabsf(theta);
+    const float t = at > 1e18f ? 0.5f / theta
+                               : copysignf(1.0f, theta) / (at + sqrtf(theta * theta + 1.0f));
+    const float c = 1.0f / sqrtf(t * t + 1.0f);
+    const float sn = t * c;
+    app = app - t * apq;
+    aqq = aqq + t * apq;
+    apq = 0.0f;
+    float x = arp, y = arq;
+    arp = c * x - sn * y;
+    arq = sn * x + c * y;
+    x = v0p; y = v0q; v0p = c * x - sn * y; v0q = sn * x + c * y;
+    x = v1p; y = v1q; v1p = c * x - sn * y; v1q = sn * x + c * y;
+    x = v2p; y = v2q; v2p = c * x - sn * y; v2q = sn * x + c * y;
+}
+
+// Unit eigenvector of the smallest eigenvalue of a symmetric 3x3 matrix, by
+// cyclic Jacobi sweeps in binary32 (pairs (0,1), (0,2), (1,2) in that order,
+// at most 8 sweeps, stopping once the off-diagonal mass is at rounding
+// level).  Its eigenvector error is ~ u ||C|| / (lambda2 - lambda3), the
+// perturbation bound itself.  The trigonometric closed form for 3x3
+// eigenvalues was tried first and dropped: in binary32 its acos step loses
+// accuracy to ~sqrt(u) when two eigenvalues nearly coincide (isotropic
+// planar patches), which the 1e-5 covariance bar exposes.  The matrix is
+// scaled by an exact power of two first; a zero matrix gives e_z.
+__host__ __device__ float3 min_eigvec(float a00, float a01, float a02, float a11, float a12, float a22) {
     const float amax = fmaxf(fmaxf(fabsf(a00), fabsf(a11)),
                              fmaxf(fabsf(a22), fmaxf(fmaxf(fabsf(a01), fabsf(a02)), fabsf(a12))));
     if (!(amax > 0.0f) || !isfinite(amax)) return make_float3(0.0f, 0.0f, 1.0f);
@@ -348,58 +368,23 @@ __device__ float3 min_eigvec(float a00, float a01, float a02, float a11, float a
     frexpf(amax, &e);
     const float sc = ldexpf(1.0f, -e);
     a00 *= sc; a01 *= sc; a02 *= sc; a11 *= sc; a12 *= sc; a22 *= sc;
-    const float q = (a00 + a11 + a22) / 3.0f;
-    const float b00 = a00 - q, b11 = a11 - q, b22 = a22 - q;
-    const float p1 = a01 * a01 + a02 * a02 + a12 * a12;
-    const float p2 = b00 * b00 + b11 * b11 + b22 * b22 + 2.0f * p1;
-    if (!(p2 > 0.0f)) return make_float3(0.0f, 0.0f, 1.0f);
-    const float p = sqrtf(p2 / 6.0f);
-    const float ip = 1.0f / p;
-    const float c00 = b00 * ip, c11 = b11 * ip, c22 = b22 * ip;
-    const float c01 = a01 * ip, c02 = a02 * ip, c12 = a12 * ip;
-    const float det = c00 * (c11 * c22 - c12 * c12) - c01 * (c01 * c22 - c12 * c02) +
-                      c02 * (c01 * c12 - c11 * c02);
-    const float r = fminf(fmaxf(0.5f * det, -1.0f), 1.0f);
-    const float phi = acosf(r) / 3.0f;
-    const float lmin = q + 2.0f * p * cosf(phi + 2.09439510239319549f);
-    const float3 r0 = make_float3(a00 - lmin, a01, a02);
-    const float3 r1 = make_float3(a01, a11 - lmin, a12);
-    const float3 r2 = make_float3(a02, a12, a22 - lmin);
-    float3 best = cross3(r0, r1);
-    float db = dot3(best, best);
-    {
-        const float3 x = cross3(r0, r2);
-        const float d = dot3(x, x);
-        if (d > db) { best = x; db = d; }
+    float v00 = 1.0f, v01 = 0.0f, v02 = 0.0f;
+    float v10 = 0.0f, v11 = 1.0f, v12 = 0.0f;
+    float v20 = 0.0f, v21 = 0.0f, v22 = 1.0f;
+    for (int sweep = 0; sweep < 8; ++sweep) {
+        const float off = a01 * a01 + a02 * a02 + a12 * a12;
+        const float dia = a00 * a00 + a11 * a11 + a22 * a22;
+        if (!(off > 1e-15f * dia)) break;
+        jacobi_rotate(a00, a11, a01, a02, a12, v00, v01, v10, v11, v20, v21);  // (0,1), r = 2
+        jacobi_rotate(a00, a22, a02, a01, a12, v00, v02, v10, v12, v20, v22);  // (0,2), r = 1
+        jacobi_rotate(a11, a22, a12, a01, a02, v01, v02, v11, v12, v21, v22);  // (1,2), r = 0
     }
-    {
-        const float3 x = cross3(r1, r2);
-        const float d = dot3(x, x);
-        if (d > db) { best = x; db = d; }
-    }
-    if (db > 1e-24f) {
-        const float inv = 1.0f / sqrtf(db);
-        return make_float3(best.x * inv, best.y * inv, best.z * inv);
-    }
-    float3 rm = r0;
-    float nm = dot3(r0, r0);
-    {
-        const float d = dot3(r1, r1);
-        if (d > nm) { rm = r1; nm = d; }
-    }
-    {
-        const float d = dot3(r2, r2);
-        if (d > nm) { rm = r2; nm = d; }
-    }
-    if (nm > 1e-24f) {
-        const float ax = fabsf(rm.x), ay = fabsf(rm.y), az = fabsf(rm.z);
-        const float3 ea = (ax <= ay && ax <= az) ? make_float3(1.0f, 0.0f, 0.0f)
-                          : (ay <= az ? make_float3(0.0f, 1.0f, 0.0f) : make_float3(0.0f, 0.0f, 1.0f));
-        const float3 v = cross3(rm, ea);
-        const float inv = 1.0f / sqrtf(dot3(v, v));
-        return make_float3(v.x * inv, v.y * inv, v.z * inv);
-    }
-    return make_float3(0.0f, 0.0f, 1.0f);
+    float3 n = make_float3(v00, v10, v20);
+    float lmin = a00;
+    if (a11 < lmin) { lmin = a11; n = make_float3(v01, v11, v21); }
+    if (a22 < lmin) { n = make_float3(v02, v12, v22); }
+    const float inv = 1.0f / sqrtf(n.x * n.x + n.y * n.y + n.z * n.z);
+    return make_float3(n.x * inv, n.y * inv, n.z * inv);
 }
 
 // Covariance of one neighbourhood row (Sec. III-C1, C_i of Eq. 19).

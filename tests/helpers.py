@@ -34,7 +34,8 @@ def check_regularised_cov(gpu6, ref6, raw_ref6, raw_gpu6, eps, rtol=COV_RTOL):
     eigenvector, so its error grows as 1/gap (Davis-Kahan: sin(theta) <=
     ||dC|| / (lambda2 - lambda3)); where the binary32 covariance error dC
     (measured, raw_gpu6 vs raw_ref6) over the eigen-gap allows more, the
-    bound becomes rtol ||C'|| + 4 (||dC||_F + 1e-7 ||C||_F) / gap.  Rows with
+    bound becomes rtol ||C'|| + 4 (||dC||_F + 1e-6 ||C||_F) / gap, the 1e-6
+    covering the binary32 eigen-solve itself (~16u).  Rows with
     a repeated smallest eigenvalue (gap ~ 0) accept any unit normal from its
     eigenspace: C'_gpu must have eigenvalues {eps, 1, 1} and n^T C n within
     1e-6 tr(C) of lambda_min.  Returns the fraction of rows held to the plain
@@ -48,7 +49,7 @@ def check_regularised_cov(gpu6, ref6, raw_ref6, raw_gpu6, eps, rtol=COV_RTOL):
     cnorm = full_frob(raw_ref6)
     err = full_frob(gpu6 - ref6)
     base = rtol * full_frob(ref6)
-    dk = 4.0 * (dC + 1e-7 * cnorm) / np.maximum(gap, 1e-300)
+    dk = 4.0 * (dC + 1e-6 * cnorm) / np.maximum(gap, 1e-300)
     plain = err <= base
     degenerate = gap <= 1e-6 * tr
     ok = plain | ((~degenerate) & (err <= base + dk))

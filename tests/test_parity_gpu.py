@@ -299,9 +299,9 @@ def test_c2_full_size_sampled_parity(c2, gpu_lib):
     assert frac > 0.97
     # every row: valid, ascending keys, d2 consistent with the returned points
     assert (idx >= 0).all() and (idx < len(m)).all()
-    key = d2.astype(np.float64) * 2.0 ** 32 + idx
+    key = (d2.view(np.uint32).astype(np.uint64) << np.uint64(32)) | idx.astype(np.uint64)
     assert (np.diff(d2, axis=1) >= 0).all()
-    assert (np.diff(key, axis=1) > 0).all()
+    assert (key[:, 1:] > key[:, :-1]).all()
     diff = q[:, None, :].astype(np.float64) - m[idx].astype(np.float64)
     np.testing.assert_allclose(d2, (diff ** 2).sum(-1), rtol=1e-5, atol=1e-9)
 
