@@ -278,6 +278,7 @@ def main():
     clk = clocks.stop()
     st = t.sync_status(stream)
     assert st == pc.PC_OK, pc.pc_status_string(st)
+    path_stats = t.stats(reset=True, stream=stream)
     ms = [a.elapsed_time(b) for a, b in ev]
     total_ms = sum(ms)
     if dist:
@@ -352,6 +353,9 @@ def main():
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 12 * N,
                     "d2h_bytes_per_step": N * (8 * K_NN + 24)},
             "clocks": clk,
+            "search_paths": {"queries": path_stats["queries"],
+                             "warp_search_frac": path_stats["warp_search"] / max(1, path_stats["queries"]),
+                             "exhaustive": path_stats["exhaustive"]},
             "gpu_launches": args.steps,
         }
         if base is not None:

@@ -80,10 +80,12 @@ typedef struct {
 
 /* Launch shape of the search kernel.  None of these changes any result. */
 typedef struct {
-    int tile;          /* queries per warp work item, 1..32; <= 0: 32 */
-    int warps;         /* warps per block, 1..16; <= 0: 4 */
-    float rho_scale;   /* first search radius = rho_scale x the previous query's k-th
-                          distance (or the target's calibrated radius); <= 0: 1.15 */
+    int tile;          /* queries per warp work item (one per lane for k <= 32), 1..32;
+                          <= 0: 32 */
+    int warps;         /* warps per block, 1..8; <= 0: 4 */
+    float rho_scale;   /* scales the target's calibrated k-th-neighbour radius that the
+                          search starts from (k <= 32: trial radii 0.7..1.75 x it);
+                          <= 0: 1.0 */
 } pc_tune;
 
 /* What the built target looks like (for reporting and tuning). */
@@ -98,6 +100,16 @@ typedef struct {
     int64_t device_bytes; /* device memory held by the handle */
     float rho_hint[64]; /* calibrated first search radius for k = 1..64 (0 if k > M) */
 } pc_target_info;
+
+/* Counters kept by the search kernels since the last reset (one atomic per
+ * warp work item; they never change a result). */
+typedef struct {
+    int64_t queries;     /* queries answered */
+    int64_t warp_search; /* of those, answered by the warp-cooperative search
+                            (k > 32, or k <= 32 queries the lane path handed over) */
+    int64_t exhaustive;  /* searches that ended in the exhaustive cell scan */
+    int64_t reserved;
+} pc_stats;
 
 /* One scan of a batch: device pointers, caller-owned. */
 typedef struct {
@@ -156,6 +168,10 @@ PC_API pc_status pc_knn_cov(pc_target t, const float *q_dev, int64_t N, int k, f
  * pc_sync_status needed). */
 PC_API pc_status pc_knn_cov_host(pc_target t, const float *q_host, int64_t N, int k, float eps,
                           int32_t *idx_host, float *d2_host, float *cov_host, pc_stream s);
+
+/* Synchronises `s` and copies the target's counters to *out; reset != 0
+ * zeroes them afterwards. */
+PC_API pc_status pc_get_stats(pc_target t, pc_stream s, pc_stats *out, int reset);
 
 /* Synchronises `s`, returns and clears the target's status word: PC_OK, or
  * the first of PC_ERR_NONFINITE, PC_ERR_SEARCH_LIMIT, PC_ERR_BAD_INDEX raised

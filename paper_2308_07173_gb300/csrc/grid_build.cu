@@ -352,6 +352,23 @@ __global__ void k_hash_insert(const u64* __restrict__ cell_keys,
     }
 }
 
+__global__ void k_occ_set(const u64* __restrict__ cell_keys, int64_t U, int bx, int by, int dimx,
+                          int dimy, uint32_t* occ) {
+    const int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (u >= U) return;
+    const u64 key = cell_keys[u];
+    const int64_t cx = (int64_t)(key & ((1ull << bx) - 1ull));
+    const int64_t cy = (int64_t)((key >> bx) & ((1ull << by) - 1ull));
+    const int64_t cz = (int64_t)(key >> (bx + by));
+    const int64_t L = cx + (int64_t)dimx * (cy + (int64_t)dimy * cz);
+    atomicOr(&occ[L >> 5], 1u << (uint32_t)(L & 31));
+}
+
+__global__ void k_popc(const uint32_t* __restrict__ occ, int64_t nw, uint32_t* __restrict__ out) {
+    const int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (w < nw) out[w] = (uint32_t)__popc(occ[w]);
+}
+
 __global__ void k_gather(const float* __restrict__ xyz, const uint32_t* __restrict__ vals,
                          int64_t n, float4* __restrict__ pts, float4* __restrict__ xyz4) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -434,7 +451,8 @@ cudaError_t count_cells(const float* xyz, int64_t M, const float o[3], float h, 
 }  // namespace
 
 void pc_free_grid(pc_target_s* t) {
-    void* ps[] = {t->table, t->pts, t->xyz, t->cell_keys, t->cell_start, t->status, t->stage};
+    void* ps[] = {t->table, t->pts, t->xyz, t->cell_keys, t->cell_start, t->status, t->stage,
+                  t->occ, t->rank};
     for (void* p : ps)
         if (p) cudaFree(p);
     t->table = nullptr;
@@ -442,6 +460,8 @@ void pc_free_grid(pc_target_s* t) {
     t->cell_keys = nullptr;
     t->cell_start = nullptr;
     t->status = nullptr;
+    t->occ = nullptr;
+    t->rank = nullptr;
     t->stage = nullptr;
     t->stage_bytes = 0;
 }
@@ -456,8 +476,9 @@ pc_status pc_build_grid(const float* xyz, int64_t M, const pc_build_opts& opts, 
                         pc_target_s* t) {
     Scratch sc;
     // persistent small buffers first
-    PC_TRY(cudaMalloc(&t->status, sizeof(int) * 4));
-    PC_TRY(cudaMemsetAsync(t->status, 0, sizeof(int) * 4, s));
+    // status word + statistics counters (64 bytes)
+    PC_TRY(cudaMalloc(&t->status, 64));
+    PC_TRY(cudaMemsetAsync(t->status, 0, 64, s));
 
     // 1. bbox + finite check
     unsigned* bb = sc.alloc<unsigned>(8);
@@ -564,6 +585,23 @@ pc_status pc_build_grid(const float* xyz, int64_t M, const pc_build_opts& opts, 
                                                     log2cap);
     PC_TRY(cudaGetLastError());
 
+    // 6b. row index: occupancy bitmap over the grid + rank per 32-cell word
+    const int64_t ngrid = (int64_t)dims[0] * dims[1] * dims[2];
+    int64_t nwords = 0;
+    if (ngrid <= ((int64_t)1 << 36)) {
+        nwords = (ngrid + 31) / 32;
+        PC_TRY(cudaMalloc(&t->occ, sizeof(uint32_t) * (size_t)nwords));
+        PC_TRY(cudaMalloc(&t->rank, sizeof(uint32_t) * (size_t)nwords));
+        uint32_t* pop = sc.alloc<uint32_t>(nwords);
+        uint32_t* tot2 = sc.alloc<uint32_t>(1);
+        if (!pop || !tot2) return pc_from_cuda(sc.err);
+        PC_TRY(cudaMemsetAsync(t->occ, 0, sizeof(uint32_t) * (size_t)nwords, s));
+        k_occ_set<<<grid_for(U, 256), 256, 0, s>>>(t->cell_keys, U, bx, by, dims[0], dims[1], t->occ);
+        k_popc<<<grid_for(nwords, 256), 256, 0, s>>>(t->occ, nwords, pop);
+        PC_TRY(cudaGetLastError());
+        PC_TRY(scan_exclusive(pop, t->rank, nwords, tot2, sc, s));
+    }
+
     // 7. float4 copies
     PC_TRY(cudaMalloc(&t->pts, sizeof(float4) * (size_t)M));
     PC_TRY(cudaMalloc(&t->xyz, sizeof(float4) * (size_t)M));
@@ -593,8 +631,12 @@ pc_status pc_build_grid(const float* xyz, int64_t M, const pc_build_opts& opts, 
     g.xyz = t->xyz;
     g.cell_keys = t->cell_keys;
     g.cell_start = t->cell_start;
+    g.occ = t->occ;
+    g.rank = t->rank;
     g.status = t->status;
+    g.stats = reinterpret_cast<unsigned long long*>(reinterpret_cast<char*>(t->status) + 32);
     t->device_bytes = (int64_t)(sizeof(uint4) * t->table_cap + 2 * sizeof(float4) * M +
-                                sizeof(u64) * U + sizeof(uint32_t) * (U + 1) + 4 * sizeof(int));
+                                sizeof(u64) * U + sizeof(uint32_t) * (U + 1) + 64 +
+                                2 * sizeof(uint32_t) * nwords);
     return PC_OK;
 }

@@ -317,6 +317,7 @@ __device__ bool knn_search(const Grid& g, float qx, float qy, float qz, int k, f
         rho = fminf(fmaxf(rho, 1e-3f * g.h) * f, 1e30f);
     }
     if (!g.exhaustive) return false;
+    if (lane == 0) atomicAdd(&g.stats[2], 1ull);
     state_reset(S);
     scan_all_cells(g, qx, qy, qz, S, pend, k, lane);
     flush(S, pend, k, lane);
@@ -392,14 +393,14 @@ __host__ __device__ float3 min_eigvec(float a00, float a01, float a02, float a11
 // so the sums stay small: mean m of (p_j - p0), then the centred moments of
 // (p_j - p0) - m, divided by k.  Built with --fmad=false, so every + and *
 // below is rounded once and the fused and standalone kernels agree bit for
-// bit.  `check`: validate every index (pc_cov); otherwise a leading -1
-// marks an unanswered row.
-__device__ void cov_row(const Grid& g, const int32_t* nb, int k, float eps, float* out,
+// bit.  The row is nb[0], nb[st], ..., nb[(k-1) st].  `check`: validate
+// every index (pc_cov); otherwise a leading -1 marks an unanswered row.
+__device__ void cov_row(const Grid& g, const int32_t* nb, int st, int k, float eps, float* out,
                         bool check) {
     bool bad = nb[0] < 0;
     if (check) {
         bool oob = false;
-        for (int j = 0; j < k; ++j) oob |= (nb[j] < 0) || ((int64_t)nb[j] >= g.m);
+        for (int j = 0; j < k; ++j) oob |= (nb[j * st] < 0) || ((int64_t)nb[j * st] >= g.m);
         if (oob) atomicOr(g.status, ST_BAD_INDEX);
         bad = oob;
     }
@@ -411,7 +412,7 @@ __device__ void cov_row(const Grid& g, const int32_t* nb, int k, float eps, floa
     const float4 p0 = __ldg(&g.xyz[nb[0]]);
     float sx = 0.0f, sy = 0.0f, sz = 0.0f;
     for (int j = 0; j < k; ++j) {
-        const float4 p = __ldg(&g.xyz[nb[j]]);
+        const float4 p = __ldg(&g.xyz[nb[j * st]]);
         sx = sx + (p.x - p0.x);
         sy = sy + (p.y - p0.y);
         sz = sz + (p.z - p0.z);
@@ -420,7 +421,7 @@ __device__ void cov_row(const Grid& g, const int32_t* nb, int k, float eps, floa
     const float mx = sx / fk, my = sy / fk, mz = sz / fk;
     float cxx = 0.0f, cxy = 0.0f, cxz = 0.0f, cyy = 0.0f, cyz = 0.0f, czz = 0.0f;
     for (int j = 0; j < k; ++j) {
-        const float4 p = __ldg(&g.xyz[nb[j]]);
+        const float4 p = __ldg(&g.xyz[nb[j * st]]);
         const float dx = (p.x - p0.x) - mx;
         const float dy = (p.y - p0.y) - my;
         const float dz = (p.z - p0.z) - mz;
@@ -454,88 +455,385 @@ struct TileArgs {
     float rho_scale;
 };
 
-// Per-warp shared memory: 64 staged survivor keys, then (fused form) the
-// tile's neighbour indices, row stride k|1 (odd, so the epilogue's
-// lane-per-row reads hit distinct banks).
-__host__ __device__ __forceinline__ int idx_stride(int k) { return k | 1; }
-__host__ __device__ __forceinline__ size_t warp_smem_bytes(int k, bool cov) {
-    size_t b = 64 * sizeof(u64);
-    if (cov) b += (size_t)32 * idx_stride(k) * sizeof(int32_t);
-    return (b + 15) & ~(size_t)15;
+// Per-warp shared memory: 64 staged survivor keys of the warp-cooperative
+// search, then the lane path's survivor lists: 32 slots x 32 lanes of
+// positions into pts ([slot][lane], so a slot is one 128-byte row).
+constexpr int LANE_CAP = 32;  // survivors the lane path can sort
+__host__ __device__ __forceinline__ size_t warp_smem_bytes() {
+    return 64 * sizeof(u64) + (size_t)LANE_CAP * 32 * sizeof(uint32_t);
 }
 
-template <int SLOTS, bool COV>
-__device__ void process_tile(const Grid& g, const float* __restrict__ q, int64_t n0, int cnt,
-                             const TileArgs& a, int32_t* __restrict__ idx, float* __restrict__ d2,
-                             float* __restrict__ cov, float& rho, u64* pend, int32_t* sidx,
-                             int lane) {
+__device__ __forceinline__ void cas32(uint32_t& a, uint32_t& b) {
+    const uint32_t lo = min(a, b), hi = max(a, b);
+    a = lo;
+    b = hi;
+}
+
+// Bitonic sort network over the first NN registers, ascending.
+template <int NN>
+__device__ __forceinline__ void sort_regs(uint32_t (&K)[LANE_CAP]) {
+#pragma unroll
+    for (int size = 2; size <= NN; size <<= 1)
+#pragma unroll
+        for (int stride = size >> 1; stride > 0; stride >>= 1)
+#pragma unroll
+            for (int i = 0; i < NN; ++i) {
+                const int j = i ^ stride;
+                if (j > i) {
+                    if ((i & size) == 0) cas32(K[i], K[j]);
+                    else cas32(K[j], K[i]);
+                }
+            }
+}
+
+// Trial radii of the lane path, as multiples of the starting radius: a
+// geometric ladder with ratio 1.1 (so the count at the chosen radius is at
+// most ~1.2x the smallest count that reaches k on a surface).
+constexpr int NRAD = 8;
+__device__ __forceinline__ float rad_mul(int j) {
+    return j == 0 ? 0.75f : j == 1 ? 0.83f : j == 2 ? 0.91f : j == 3 ? 1.0f
+         : j == 4 ? 1.1f : j == 5 ? 1.21f : j == 6 ? 1.33f : 1.46f;
+}
+
+// Visit every point of the cell box [l, h] (clamped to the grid) whose
+// cell can hold a point within sqrt(tmax) of q, as f(position, point).
+// Rows along x are pruned by a conservative lower bound (the eta margin of
+// certified_tau); each surviving cell is a hash lookup.
+template <typename F>
+__device__ __forceinline__ void for_box_points(const Grid& g, float qx, float qy, float qz, int lx,
+                                               int hx, int ly, int hy, int lz, int hz, float eta,
+                                               float tmax, F&& f) {
+    for (int cz = lz; cz <= hz; ++cz) {
+        const float zl = g.oz + (float)cz * g.h, zh = g.oz + (float)(cz + 1) * g.h;
+        const float gz = fmaxf(fmaxf(zl - qz, qz - zh), 0.0f) - eta;
+        const float gz2 = gz > 0.0f ? gz * gz : 0.0f;
+        for (int cy = ly; cy <= hy; ++cy) {
+            const float yl = g.oy + (float)cy * g.h, yh = g.oy + (float)(cy + 1) * g.h;
+            const float gy = fmaxf(fmaxf(yl - qy, qy - yh), 0.0f) - eta;
+            const float gyz2 = gz2 + (gy > 0.0f ? gy * gy : 0.0f);
+            if (gyz2 * (1.0f - 0x1p-20f) > tmax) continue;
+            for (int cx = lx; cx <= hx; ++cx) {
+                const float xl = g.ox + (float)cx * g.h, xh = g.ox + (float)(cx + 1) * g.h;
+                const float gx = fmaxf(fmaxf(xl - qx, qx - xh), 0.0f) - eta;
+                const float lb2 = gyz2 + (gx > 0.0f ? gx * gx : 0.0f);
+                if (lb2 * (1.0f - 0x1p-20f) > tmax) continue;
+                const uint2 r = lookup_cell(g, pack_key(cx, cy, cz, g.bx, g.by));
+                for (uint32_t i = 0; i < r.y; ++i) f(r.x + i, __ldg(&g.pts[r.x + i]));
+            }
+        }
+    }
+}
+
+// The part of row (cy, cz) that can hold a point within sqrt(tmax) of q, as
+// a range of pts through the row index: the row is skipped when the lower
+// bound of dy^2 + dz^2 exceeds tmax, else narrowed along x to half-width
+// sqrt(tmax (1 + 2^-18) - that bound) widened by eta (the cell rule's
+// rounding).  A point outside the range has a binary32 d2 above tmax.
+__device__ __forceinline__ uint2 row_part(const Grid& g, float qx, float qy, float qz, int cy,
+                                          int cz, int lx, int hx, float eta, float tmax, float tx) {
+    const float zl = g.oz + (float)cz * g.h, zh = g.oz + (float)(cz + 1) * g.h;
+    const float gz = fmaxf(fmaxf(zl - qz, qz - zh), 0.0f) - eta;
+    const float yl = g.oy + (float)cy * g.h, yh = g.oy + (float)(cy + 1) * g.h;
+    const float gy = fmaxf(fmaxf(yl - qy, qy - yh), 0.0f) - eta;
+    const float gyz2 = (gz > 0.0f ? gz * gz : 0.0f) + (gy > 0.0f ? gy * gy : 0.0f);
+    if (gyz2 * (1.0f - 0x1p-20f) > tmax) return make_uint2(0u, 0u);
+    const float xw = sqrtf(fmaxf(tx - gyz2, 0.0f)) + eta;
+    const int x0 = max(lx, cell_of(__fsub_rn(qx, xw), g.ox, g.inv_h));
+    const int x1 = min(hx, cell_of(__fadd_rn(qx, xw), g.ox, g.inv_h));
+    if (x0 > x1) return make_uint2(0u, 0u);
+    return row_range(g, cy, cz, x0, x1);
+}
+
+// Same visit as for_box_points through the row index: every row of the box
+// is one contiguous range of pts.  Rows are resolved two at a time so their
+// index loads overlap.
+template <typename F>
+__device__ __forceinline__ void for_rows(const Grid& g, float qx, float qy, float qz, int lx, int hx,
+                                         int ly, int hy, int lz, int hz, float eta, float tmax,
+                                         F&& f) {
+    const float tx = tmax * (1.0f + 0x1p-18f);
+    int cy = ly, cz = lz;
+    while (cz <= hz) {
+        const int cy2 = cy < hy ? cy + 1 : ly;
+        const int cz2 = cy < hy ? cz : cz + 1;
+        const uint2 ra = row_part(g, qx, qy, qz, cy, cz, lx, hx, eta, tmax, tx);
+        const uint2 rb = cz2 <= hz ? row_part(g, qx, qy, qz, cy2, cz2, lx, hx, eta, tmax, tx)
+                                   : make_uint2(0u, 0u);
+        for (uint32_t i = 0; i < ra.y; ++i) f(ra.x + i, __ldg(&g.pts[ra.x + i]));
+        for (uint32_t i = 0; i < rb.y; ++i) f(rb.x + i, __ldg(&g.pts[rb.x + i]));
+        cy = cy2 < hy ? cy2 + 1 : ly;
+        cz = cy2 < hy ? cz2 : cz2 + 1;
+    }
+}
+
+// (d2, index) key of the survivor in a lane's slot, recomputed from pts.
+__device__ __forceinline__ u64 slot_key(const Grid& g, const uint32_t* posl, int slot, int lane,
+                                        float qx, float qy, float qz) {
+    const float4 p = __ldg(&g.pts[posl[slot * 32 + lane]]);
+    const float d = sqdist_pinned(qx, qy, qz, p.x, p.y, p.z);
+    return ((u64)__float_as_uint(d) << 32) | (u64)__float_as_uint(p.w);
+}
+
+// k <= 32: one query per lane.  Pass 1 counts, for each trial radius
+// r_j = m_j rho0, the target points with d2 <= t_j = min(r_j^2, tau), tau
+// certified for the box around the largest radius; the smallest t_j that
+// holds >= k points (and at most 32) is exact by the same argument as the
+// warp search: every point with d2 <= t_j lies in the box, so the k
+// smallest of those are the k smallest overall.  Pass 2 collects their
+// positions in the lane's shared-memory list.  They are ordered by a
+// register bitonic network on 32-bit keys (d2 bits << 1 with the low five
+// bits replaced by the slot), which orders d2 to within 16 ulps; any run of
+// neighbours left in the same 16-ulp bucket is then put in exact (d2,
+// index) order by bubble passes on the full keys.  Lanes whose query needs
+// a wider radius, more than 32 survivors or a bigger box are finished by
+// the warp-cooperative search, one query at a time.
+template <bool COV>
+__device__ void lane_tile(const Grid& g, const float* __restrict__ q, int64_t n0, int cnt,
+                          const TileArgs& a, float rho0, int32_t* __restrict__ idx,
+                          float* __restrict__ d2, float* __restrict__ cov, u64* pend,
+                          uint32_t* posl, int lane) {
     const int k = a.k;
-    const int ks = idx_stride(k);
+    const bool active = lane < cnt;
+    const int64_t n = n0 + lane;
+    float qx = 0.0f, qy = 0.0f, qz = 0.0f;
+    if (active) {
+        qx = __ldg(q + 3 * n);
+        qy = __ldg(q + 3 * n + 1);
+        qz = __ldg(q + 3 * n + 2);
+    }
+    const bool finite = active && isfinite(qx) && isfinite(qy) && isfinite(qz);
+    bool fallback = false;
+    int m = 0;
+    float thr = -1.0f;
+    int lx = 0, hx = -1, ly = 0, hy = -1, lz = 0, hz = -1;
+    float eta = 0.0f;
+    if (finite) {
+        const float rmax = rho0 * rad_mul(NRAD - 1);
+        const int ulx = cell_of(__fsub_rn(qx, rmax), g.ox, g.inv_h);
+        const int uhx = cell_of(__fadd_rn(qx, rmax), g.ox, g.inv_h);
+        const int uly = cell_of(__fsub_rn(qy, rmax), g.oy, g.inv_h);
+        const int uhy = cell_of(__fadd_rn(qy, rmax), g.oy, g.inv_h);
+        const int ulz = cell_of(__fsub_rn(qz, rmax), g.oz, g.inv_h);
+        const int uhz = cell_of(__fadd_rn(qz, rmax), g.oz, g.inv_h);
+        const float tau = certified_tau(g, qx, qy, qz, ulx, uhx, uly, uhy, ulz, uhz);
+        {
+            const int cm = max(max(max(abs(ulx), abs(uhx + 1)), max(abs(uly), abs(uhy + 1))),
+                               max(abs(ulz), abs(uhz + 1)));
+            const float qm = fmaxf(fabsf(qx), fmaxf(fabsf(qy), fabsf(qz)));
+            eta = 0x1p-20f * (g.coord_scale + qm + (float)cm * g.h);
+        }
+        lx = max(ulx, 0); hx = min(uhx, g.dimx - 1);
+        ly = max(uly, 0); hy = min(uhy, g.dimy - 1);
+        lz = max(ulz, 0); hz = min(uhz, g.dimz - 1);
+        const int64_t ncl = (int64_t)max(hx - lx + 1, 0) * max(hy - ly + 1, 0) * max(hz - lz + 1, 0);
+        const int64_t nrows = (int64_t)max(hy - ly + 1, 0) * max(hz - lz + 1, 0);
+        if (tau < 0.0f || ncl > 4096 || nrows > 256 || (!g.occ && ncl > 256)) {
+            fallback = true;
+        } else {
+            float t[NRAD];
+            int c[NRAD];
+#pragma unroll
+            for (int j = 0; j < NRAD; ++j) {
+                const float r = rho0 * rad_mul(j);
+                t[j] = fminf(r * r, tau);
+                c[j] = 0;
+            }
+            auto count = [&](uint32_t, const float4 p) {
+                const float d = sqdist_pinned(qx, qy, qz, p.x, p.y, p.z);
+#pragma unroll
+                for (int j = 0; j < NRAD; ++j) c[j] += d <= t[j] ? 1 : 0;
+            };
+            if (g.occ) for_rows(g, qx, qy, qz, lx, hx, ly, hy, lz, hz, eta, t[NRAD - 1], count);
+            else for_box_points(g, qx, qy, qz, lx, hx, ly, hy, lz, hz, eta, t[NRAD - 1], count);
+            int js = -1;
+#pragma unroll
+            for (int j = NRAD - 1; j >= 0; --j)
+                if (c[j] >= k) js = j;
+            int cj = 0;
+            float tj = -1.0f;
+#pragma unroll
+            for (int j = 0; j < NRAD; ++j)
+                if (j == js) { cj = c[j]; tj = t[j]; }
+            if (js < 0 || cj > LANE_CAP) {
+                fallback = true;
+            } else {
+                m = cj;
+                thr = tj;
+            }
+        }
+    }
+    if (m > 0) {
+        int w = 0;
+        auto collect = [&](uint32_t pos, const float4 p) {
+            const float d = sqdist_pinned(qx, qy, qz, p.x, p.y, p.z);
+            if (d <= thr && w < LANE_CAP) {
+                posl[w * 32 + lane] = pos;
+                ++w;
+            }
+        };
+        if (g.occ) for_rows(g, qx, qy, qz, lx, hx, ly, hy, lz, hz, eta, thr, collect);
+        else for_box_points(g, qx, qy, qz, lx, hx, ly, hy, lz, hz, eta, thr, collect);
+    }
+    __syncwarp();
+    uint32_t K[LANE_CAP];
+#pragma unroll
+    for (int s = 0; s < LANE_CAP; ++s) {
+        uint32_t key = 0xffffffffu;
+        if (s < m) {
+            const float4 p = __ldg(&g.pts[posl[s * 32 + lane]]);
+            const float d = sqdist_pinned(qx, qy, qz, p.x, p.y, p.z);
+            key = ((__float_as_uint(d) << 1) & ~31u) | (uint32_t)s;
+        }
+        K[s] = key;
+    }
+    if (__reduce_max_sync(FULL, (unsigned)m) <= 16u) sort_regs<16>(K);
+    else sort_regs<LANE_CAP>(K);
+    bool amb = false;
+#pragma unroll
+    for (int r = 0; r + 1 < LANE_CAP; ++r) amb |= (r + 1 < m) && ((K[r] ^ K[r + 1]) < 32u);
+    for (int pass = 0; amb && pass < LANE_CAP; ++pass) {
+        bool swapped = false;
+#pragma unroll
+        for (int r = 0; r + 1 < LANE_CAP; ++r) {
+            if (r + 1 < m && ((K[r] ^ K[r + 1]) < 32u)) {
+                const u64 ka = slot_key(g, posl, (int)(K[r] & 31u), lane, qx, qy, qz);
+                const u64 kb = slot_key(g, posl, (int)(K[r + 1] & 31u), lane, qx, qy, qz);
+                if (kb < ka) {
+                    const uint32_t tmp = K[r];
+                    K[r] = K[r + 1];
+                    K[r + 1] = tmp;
+                    swapped = true;
+                }
+            }
+        }
+        amb = swapped;
+    }
+    if (m > 0) {
+#pragma unroll
+        for (int r = 0; r < LANE_CAP; ++r)
+            if (r < k) {
+                const u64 key = slot_key(g, posl, (int)(K[r] & 31u), lane, qx, qy, qz);
+                idx[n * k + r] = (int32_t)(uint32_t)key;
+                d2[n * k + r] = __uint_as_float((uint32_t)(key >> 32));
+            }
+    } else if (active && !finite) {
+        for (int r = 0; r < k; ++r) {
+            idx[n * k + r] = -1;
+            d2[n * k + r] = INFINITY;
+        }
+        atomicOr(g.status, ST_NONFINITE);
+    }
+    unsigned fb = __ballot_sync(FULL, fallback);
+    if (lane == 0) {
+        atomicAdd(&g.stats[0], (unsigned long long)cnt);
+        if (fb) atomicAdd(&g.stats[1], (unsigned long long)__popc(fb));
+    }
+    while (fb) {
+        const int f = __ffs(fb) - 1;
+        fb &= fb - 1u;
+        const float fx = __shfl_sync(FULL, qx, f), fy = __shfl_sync(FULL, qy, f),
+                    fz = __shfl_sync(FULL, qz, f);
+        float rho = rho0 * rad_mul(NRAD - 1);
+        SearchState<1> S;
+        state_reset(S);
+        const bool ok = knn_search<1>(g, fx, fy, fz, k, rho, S, pend, lane);
+        if (!ok && lane == 0) atomicOr(g.status, ST_SEARCH_LIMIT);
+        const int64_t nf = n0 + f;
+        if (lane < k) {
+            idx[nf * k + lane] = ok ? (int32_t)(uint32_t)S.L[0] : -1;
+            d2[nf * k + lane] = ok ? __uint_as_float((uint32_t)(S.L[0] >> 32)) : INFINITY;
+        }
+    }
+    if (COV && cov != nullptr) {
+        __syncwarp();  // orders the idx rows written by other lanes
+        if (active) cov_row(g, idx + n * k, 1, k, a.eps, cov + 6 * n, false);
+    }
+    __syncwarp();
+}
+
+// k > 32: the warp-cooperative search for each query of the tile in turn.
+template <bool COV>
+__device__ void warp_tile(const Grid& g, const float* __restrict__ q, int64_t n0, int cnt,
+                          const TileArgs& a, float rho0, int32_t* __restrict__ idx,
+                          float* __restrict__ d2, float* __restrict__ cov, u64* pend,
+                          int lane) {
+    const int k = a.k;
+    float rho = rho0;
+    if (lane == 0) {
+        atomicAdd(&g.stats[0], (unsigned long long)cnt);
+        atomicAdd(&g.stats[1], (unsigned long long)cnt);
+    }
     for (int i = 0; i < cnt; ++i) {
         const int64_t n = n0 + i;
         const float qx = __ldg(q + 3 * n), qy = __ldg(q + 3 * n + 1), qz = __ldg(q + 3 * n + 2);
         const bool finite = isfinite(qx) && isfinite(qy) && isfinite(qz);
-        SearchState<SLOTS> S;
+        SearchState<2> S;
         state_reset(S);
         bool ok = false;
-        if (finite) ok = knn_search<SLOTS>(g, qx, qy, qz, k, rho, S, pend, lane);
+        if (finite) ok = knn_search<2>(g, qx, qy, qz, k, rho, S, pend, lane);
         if (!ok && lane == 0) atomicOr(g.status, finite ? ST_SEARCH_LIMIT : ST_NONFINITE);
 #pragma unroll
-        for (int s = 0; s < SLOTS; ++s) {
+        for (int s = 0; s < 2; ++s) {
             const int r = s * 32 + lane;
             if (r < k) {
                 const u64 key = S.L[s];
                 const int32_t oi = ok ? (int32_t)(uint32_t)key : -1;
-                const float od = ok ? __uint_as_float((uint32_t)(key >> 32)) : INFINITY;
                 idx[n * k + r] = oi;
-                d2[n * k + r] = od;
-                if (COV) sidx[i * ks + r] = oi;
+                d2[n * k + r] = ok ? __uint_as_float((uint32_t)(key >> 32)) : INFINITY;
             }
         }
         if (ok) {
             const float dk = __uint_as_float((uint32_t)(S.kth >> 32));
-            rho = fminf(fmaxf(sqrtf(dk) * a.rho_scale, 1e-2f * g.h), 1e30f);
+            rho = fminf(fmaxf(sqrtf(dk) * 1.15f, 1e-2f * g.h), 1e30f);
         }
     }
     if (COV && cov != nullptr) {
         __syncwarp();
-        if (lane < cnt) cov_row(g, sidx + lane * ks, k, a.eps, cov + 6 * (n0 + lane), false);
+        if (lane < cnt) cov_row(g, idx + (n0 + lane) * k, 1, k, a.eps, cov + 6 * (n0 + lane), false);
         __syncwarp();
     }
 }
 
 template <int SLOTS, bool COV>
-__global__ void __launch_bounds__(512) k_knn(Grid g, const float* __restrict__ q, int64_t N,
+__device__ __forceinline__ void process_tile(const Grid& g, const float* __restrict__ q, int64_t n0,
+                                             int cnt, const TileArgs& a, float rho0,
+                                             int32_t* __restrict__ idx, float* __restrict__ d2,
+                                             float* __restrict__ cov, unsigned char* wsmem,
+                                             int lane) {
+    u64* pend = reinterpret_cast<u64*>(wsmem);
+    uint32_t* posl = reinterpret_cast<uint32_t*>(wsmem + 64 * sizeof(u64));
+    if (SLOTS == 1)
+        lane_tile<COV>(g, q, n0, cnt, a, rho0, idx, d2, cov, pend, posl, lane);
+    else
+        warp_tile<COV>(g, q, n0, cnt, a, rho0, idx, d2, cov, pend, lane);
+}
+
+template <int SLOTS, bool COV>
+__global__ void __launch_bounds__(256, 2) k_knn(Grid g, const float* __restrict__ q, int64_t N,
                                              int tile, TileArgs a, float rho0,
                                              int32_t* __restrict__ idx, float* __restrict__ d2,
                                              float* __restrict__ cov) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nwarps = blockDim.x >> 5;
-    unsigned char* base = smem + (size_t)warp * warp_smem_bytes(a.k, COV);
-    u64* pend = reinterpret_cast<u64*>(base);
-    int32_t* sidx = reinterpret_cast<int32_t*>(base + 64 * sizeof(u64));
     const int64_t t = (int64_t)blockIdx.x * nwarps + warp;
     const int64_t n0 = t * tile;
     if (n0 >= N) return;
     const int cnt = (int)min((int64_t)tile, N - n0);
-    float rho = rho0;
-    process_tile<SLOTS, COV>(g, q, n0, cnt, a, idx, d2, cov, rho, pend, sidx, lane);
+    process_tile<SLOTS, COV>(g, q, n0, cnt, a, rho0, idx, d2, cov,
+                             smem + (size_t)warp * warp_smem_bytes(), lane);
 }
 
 // Batched form: one persistent launch; warps pull (scan, tile) items from a
 // device counter over the scans' prefix-summed tile table.
 template <int SLOTS, bool COV>
-__global__ void __launch_bounds__(512) k_knn_batch(Grid g, const ScanDesc* __restrict__ scans,
+__global__ void __launch_bounds__(256, 2) k_knn_batch(Grid g, const ScanDesc* __restrict__ scans,
                                                    int nscans, int64_t total_tiles, int tile,
                                                    TileArgs a, float rho0,
                                                    unsigned long long* counter) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    unsigned char* base = smem + (size_t)warp * warp_smem_bytes(a.k, COV);
-    u64* pend = reinterpret_cast<u64*>(base);
-    int32_t* sidx = reinterpret_cast<int32_t*>(base + 64 * sizeof(u64));
-    float rho = rho0;
+    unsigned char* wsmem = smem + (size_t)warp * warp_smem_bytes();
     for (;;) {
         unsigned long long item = 0;
         if (lane == 0) item = atomicAdd(counter, 1ull);
@@ -549,7 +847,7 @@ __global__ void __launch_bounds__(512) k_knn_batch(Grid g, const ScanDesc* __res
         const ScanDesc sd = scans[lo];
         const int64_t n0 = ((int64_t)item - sd.tile0) * tile;
         const int cnt = (int)min((int64_t)tile, sd.n - n0);
-        process_tile<SLOTS, COV>(g, sd.q, n0, cnt, a, sd.idx, sd.d2, sd.cov, rho, pend, sidx, lane);
+        process_tile<SLOTS, COV>(g, sd.q, n0, cnt, a, rho0, sd.idx, sd.d2, sd.cov, wsmem, lane);
     }
 }
 
@@ -557,7 +855,7 @@ __global__ void k_cov(Grid g, const int32_t* __restrict__ idx, int64_t N, int k,
                       float* __restrict__ cov) {
     const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= N) return;
-    cov_row(g, idx + n * k, k, eps, cov + 6 * n, true);
+    cov_row(g, idx + n * k, 1, k, eps, cov + 6 * n, true);
 }
 
 template <typename K>
@@ -589,7 +887,7 @@ cudaError_t ensure_attrs() {
 }
 
 int clamp_tile(int t) { return t <= 0 ? 32 : (t > 32 ? 32 : t); }
-int clamp_warps(int w) { return w <= 0 ? 4 : (w > 16 ? 16 : w); }
+int clamp_warps(int w) { return w <= 0 ? 4 : (w > 8 ? 8 : w); }
 
 }  // namespace
 
@@ -601,7 +899,7 @@ cudaError_t pc_launch_knn(const pc_target_s* t, const float* q, int64_t N, int k
     const int warps = clamp_warps(t->tune.warps);
     TileArgs a{k, eps, t->tune.rho_scale > 0 ? t->tune.rho_scale : 1.15f};
     const bool with_cov = cov != nullptr;
-    const size_t smem = (size_t)warps * warp_smem_bytes(k, with_cov);
+    const size_t smem = (size_t)warps * warp_smem_bytes();
     const int64_t tiles = (N + tile - 1) / tile;
     const int64_t blocks = (tiles + warps - 1) / warps;
     const dim3 grid((unsigned)blocks), block(warps * 32);
@@ -637,7 +935,7 @@ cudaError_t pc_launch_knn_batch(const pc_target_s* t, const ScanDesc* scans_dev,
                                 float eps, bool with_cov, float rho0,
                                 unsigned long long* counter, cudaStream_t s) {
     TileArgs a{k, eps, t->tune.rho_scale > 0 ? t->tune.rho_scale : 1.15f};
-    const size_t smem = (size_t)warps * warp_smem_bytes(k, with_cov);
+    const size_t smem = (size_t)warps * warp_smem_bytes();
     const dim3 grid((unsigned)blocks), block(warps * 32);
     if (k <= 32) {
         if (with_cov) {
@@ -659,13 +957,13 @@ cudaError_t pc_launch_knn_batch(const pc_target_s* t, const ScanDesc* scans_dev,
     return cudaGetLastError();
 }
 
-size_t pc_knn_smem_per_warp(int k, bool with_cov) { return warp_smem_bytes(k, with_cov); }
+size_t pc_knn_smem_per_warp(int k, bool with_cov) { return warp_smem_bytes(); }
 
 int pc_knn_batch_blocks(int k, bool with_cov, int warps) {
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const size_t smem = (size_t)warps * warp_smem_bytes(k, with_cov);
+    const size_t smem = (size_t)warps * warp_smem_bytes();
     cudaError_t e = ensure_attrs();
     if (e != cudaSuccess) return sms;
     if (k <= 32) {

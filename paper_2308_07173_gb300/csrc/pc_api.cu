@@ -67,7 +67,7 @@ pc_status check_query_args(const pc_target_s* t, int64_t N, int k) {
 void default_tune(pc_tune* tu) {
     tu->tile = 32;
     tu->warps = 4;
-    tu->rho_scale = 1.15f;
+    tu->rho_scale = 1.0f;
 }
 
 pc_status read_and_clear_status(pc_target_s* t, cudaStream_t s) {
@@ -110,6 +110,8 @@ pc_status calibrate_rho(pc_target_s* t, cudaStream_t s) {
     if (d2) cudaFree(d2);
     if (e != cudaSuccess) return pc_from_cuda(e);
     read_and_clear_status(t, s);  // a capped search here only skips that sample
+    cudaMemsetAsync(reinterpret_cast<char*>(t->status) + 32, 0, 32, s);
+    cudaStreamSynchronize(s);
     std::vector<float> col;
     for (int kk = 0; kk < 64; ++kk) {
         t->rho_hint[kk] = 0.0f;
@@ -156,7 +158,7 @@ pc_status pc_from_cuda(cudaError_t e) {
 float pc_rho0(const pc_target_s* t, int k) {
     float r = (k >= 1 && k <= 64) ? t->rho_hint[k - 1] : 0.0f;
     if (!(r > 0.0f)) r = t->g.h;
-    const float sc = t->tune.rho_scale > 0 ? t->tune.rho_scale : 1.15f;
+    const float sc = t->tune.rho_scale > 0 ? t->tune.rho_scale : 1.0f;
     return r * sc;
 }
 
@@ -220,12 +222,12 @@ pc_status pc_set_tune(pc_target t, const pc_tune* tune) {
         default_tune(&t->tune);
         return PC_OK;
     }
-    if (tune->tile > 32 || tune->warps > 16 || !(std::isfinite(tune->rho_scale)))
+    if (tune->tile > 32 || tune->warps > 8 || !(std::isfinite(tune->rho_scale)))
         return PC_ERR_INVALID_ARG;
     t->tune = *tune;
     if (t->tune.tile <= 0) t->tune.tile = 32;
     if (t->tune.warps <= 0) t->tune.warps = 4;
-    if (t->tune.rho_scale <= 0) t->tune.rho_scale = 1.15f;
+    if (t->tune.rho_scale <= 0) t->tune.rho_scale = 1.0f;
     return PC_OK;
 }
 
@@ -328,6 +330,25 @@ pc_status pc_sync_status(pc_target t, pc_stream s) {
     return read_and_clear_status(t, (cudaStream_t)s);
 }
 
+pc_status pc_get_stats(pc_target t, pc_stream s, pc_stats* out, int reset) {
+    pc_status r = check_target(t);
+    if (r != PC_OK) return r;
+    if (!out) return PC_ERR_INVALID_ARG;
+    DeviceGuard dg(t->device);
+    cudaStream_t st = (cudaStream_t)s;
+    unsigned long long v[4] = {0, 0, 0, 0};
+    char* base = reinterpret_cast<char*>(t->status) + 32;
+    cudaError_t e = cudaMemcpyAsync(v, base, sizeof(v), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && reset) e = cudaMemsetAsync(base, 0, sizeof(v), st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return pc_from_cuda(e);
+    out->queries = (int64_t)v[0];
+    out->warp_search = (int64_t)v[1];
+    out->exhaustive = (int64_t)v[2];
+    out->reserved = (int64_t)v[3];
+    return PC_OK;
+}
+
 pc_status pc_batch_plan(pc_target t, const pc_scan* scans, int n_scans, int k, float eps,
                         pc_batch* out) {
     if (!out) return PC_ERR_INVALID_ARG;
@@ -360,7 +381,7 @@ pc_status pc_batch_plan(pc_target t, const pc_scan* scans, int n_scans, int k, f
     b->eps = eps;
     b->with_cov = any_cov;
     b->tile = std::min(std::max(t->tune.tile, 1), 32);
-    b->warps = std::min(std::max(t->tune.warps, 1), 16);
+    b->warps = std::min(std::max(t->tune.warps, 1), 8);
     std::vector<ScanDesc> hs(n_scans);
     int64_t tiles = 0, queries = 0;
     for (int i = 0; i < n_scans; ++i) {

@@ -39,7 +39,14 @@ struct Grid {
     const float4* xyz;      // caller order: (x, y, z, 0)
     const unsigned long long* cell_keys;  // occupied cell keys, ascending [ncells]
     const uint32_t* cell_start;           // [ncells + 1] into pts
+    // Row index (null when the grid is too large for it): bit L of occ is
+    // set when cell L = cx + dimx (cy + dimy cz) is occupied, rank[w] counts
+    // the set bits in words before w.  Occupied cells are ordered by L, so a
+    // run of cells along x maps to one contiguous range of pts.
+    const uint32_t* occ;
+    const uint32_t* rank;
     int* status;
+    unsigned long long* stats;  // [0] queries, [1] warp-search fallbacks, [2] exhaustive scans
 };
 
 __device__ __forceinline__ int cell_of(float v, float o, float inv_h) {
@@ -72,6 +79,24 @@ __device__ __forceinline__ uint2 lookup_cell(const Grid& g, unsigned long long k
         slot = (slot + 1u) & mask;
     }
     return make_uint2(0u, 0u);
+}
+
+// Points of the occupied cells x0..x1 (x0 <= x1) of row (cy, cz) as one
+// range (start, count) of pts, through the row index.
+__device__ __forceinline__ uint2 row_range(const Grid& g, int cy, int cz, int x0, int x1) {
+    const int64_t base = (int64_t)g.dimx * ((int64_t)cy + (int64_t)g.dimy * cz);
+    const int64_t L0 = base + x0, L1 = base + x1;
+    const int64_t w0 = L0 >> 5, w1 = L1 >> 5;
+    const uint32_t o0 = __ldg(&g.occ[w0]);
+    const uint32_t r0 = __ldg(&g.rank[w0]);
+    const uint32_t u0 = r0 + __popc(o0 & ((1u << (uint32_t)(L0 & 31)) - 1u));
+    const uint32_t b1 = (uint32_t)(L1 & 31);
+    const uint32_t upto = b1 == 31u ? 0xffffffffu : ((2u << b1) - 1u);
+    const uint32_t u1 = (w1 == w0) ? r0 + __popc(o0 & upto)
+                                   : __ldg(&g.rank[w1]) + __popc(__ldg(&g.occ[w1]) & upto);
+    if (u1 == u0) return make_uint2(0u, 0u);
+    const uint32_t s = __ldg(&g.cell_start[u0]);
+    return make_uint2(s, __ldg(&g.cell_start[u1]) - s);
 }
 
 // The pinned binary32 squared distance: fmaf(dz,dz, fmaf(dy,dy, dx*dx)).

@@ -37,7 +37,9 @@ struct pc_target_s {
     float4* xyz;
     unsigned long long* cell_keys;
     uint32_t* cell_start;
-    int* status;
+    uint32_t* occ;
+    uint32_t* rank;
+    int* status;  // 64 bytes: status word, then 4 u64 statistics counters at +32
     // staging for pc_knn_cov_host, grown on demand
     void* stage;
     size_t stage_bytes;

@@ -82,6 +82,11 @@ class pc_target_info(ctypes.Structure):
     ]
 
 
+class pc_stats(ctypes.Structure):
+    _fields_ = [("queries", ctypes.c_int64), ("warp_search", ctypes.c_int64),
+                ("exhaustive", ctypes.c_int64), ("reserved", ctypes.c_int64)]
+
+
 class pc_scan(ctypes.Structure):
     _fields_ = [
         ("q_dev", ctypes.c_void_p),
@@ -105,6 +110,7 @@ SIGNATURES = {
     "pc_knn_cov": (_INT, [_VP, _VP, _I64, _INT, _F, _VP, _VP, _VP, _VP]),
     "pc_knn_cov_host": (_INT, [_VP, _VP, _I64, _INT, _F, _VP, _VP, _VP, _VP]),
     "pc_sync_status": (_INT, [_VP, _VP]),
+    "pc_get_stats": (_INT, [_VP, _VP, ctypes.POINTER(pc_stats), _INT]),
     "pc_batch_plan": (_INT, [_VP, ctypes.POINTER(pc_scan), _INT, _INT, _F, ctypes.POINTER(_VP)]),
     "pc_batch_run": (_INT, [_VP, _VP]),
     "pc_batch_destroy": (None, [_VP]),
@@ -187,6 +193,12 @@ def pc_knn_cov_host(t, q_host, N, k, eps, idx_host, d2_host, cov_host, stream) -
 
 def pc_sync_status(t, stream) -> int:
     return load().pc_sync_status(t, stream)
+
+
+def pc_get_stats(t, stream, reset: bool = False) -> pc_stats:
+    st = pc_stats()
+    _check(load().pc_get_stats(t, stream, ctypes.byref(st), 1 if reset else 0), "pc_get_stats")
+    return st
 
 
 def pc_batch_plan(t, scans: Sequence[pc_scan], k: int, eps: float) -> int:
@@ -335,6 +347,10 @@ class Target:
         rc = pc_knn_cov_host(self.handle, qp, n, k, float(eps), ptrs[0], ptrs[1], ptrs[2], _stream_handle(stream))
         _check(rc, "pc_knn_cov_host")
         return out
+
+    def stats(self, reset: bool = False, stream=None) -> dict:
+        st = pc_get_stats(self.handle, _stream_handle(stream), reset)
+        return {"queries": st.queries, "warp_search": st.warp_search, "exhaustive": st.exhaustive}
 
     def sync_status(self, stream=None) -> int:
         return pc_sync_status(self.handle, _stream_handle(stream))

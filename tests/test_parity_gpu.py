@@ -103,6 +103,17 @@ def test_ragged_sizes_and_k(c1, gpu_lib, n, k):
     H.check_raw_cov(cov, oracle.cov(p, ri, -1.0))
 
 
+def test_stats_count_every_query(c1, gpu_lib):
+    p, t = c1
+    t.stats(reset=True)
+    t.knn_cov(dev(p[:1000]), 10, 1e-3)
+    t.knn(dev(p[:77]), 40)
+    st = t.stats(reset=True)
+    assert st["queries"] == 1077
+    assert 77 <= st["warp_search"] <= 1077  # k > 32 always takes the warp search
+    assert t.stats()["queries"] == 0
+
+
 def test_empty_query_is_noop(c1, gpu_lib):
     _, t = c1
     q = torch.empty((0, 3), dtype=torch.float32, device="cuda")
@@ -111,7 +122,7 @@ def test_empty_query_is_noop(c1, gpu_lib):
     assert t.sync_status() == gpu_lib.PC_OK
 
 
-@pytest.mark.parametrize("tune", [(1, 1, 0.5), (7, 3, 3.0), (32, 16, 1.0), (16, 8, 20.0)])
+@pytest.mark.parametrize("tune", [(1, 1, 0.5), (7, 3, 3.0), (32, 8, 1.0), (16, 8, 20.0), (32, 2, 0.2)])
 def test_launch_shape_never_changes_results(c1, gpu_lib, tune):
     p, t = c1
     q = dev(p[::5])
