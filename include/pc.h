@@ -71,7 +71,7 @@ typedef enum {
 typedef struct {
     float cell_size;   /* > 0: voxel edge h in the caller's units; <= 0: chosen so the
                           mean points per occupied cell is about `occupancy` */
-    float occupancy;   /* target mean points per occupied cell for the automatic h; <= 0: 6 */
+    float occupancy;   /* target mean points per occupied cell for the automatic h; <= 0: 12 */
     float hash_load;   /* open-addressing load factor in (0, 0.9]; <= 0: 0.5 */
     int max_box_cells; /* the radius-widening search stops growing its cell box here; <= 0: 4096 */
     int exhaustive;    /* past max_box_cells: 1 = exact scan of every occupied cell,
@@ -85,7 +85,7 @@ typedef struct {
     int warps;         /* warps per block, 1..8; <= 0: 4 */
     float rho_scale;   /* scales the target's calibrated k-th-neighbour radius that the
                           search starts from (k <= 32: trial radii 0.7..1.75 x it);
-                          <= 0: 1.0 */
+                          <= 0: 0.9 */
 } pc_tune;
 
 /* What the built target looks like (for reporting and tuning). */

@@ -522,7 +522,7 @@ pc_status pc_build_grid(const float* xyz, int64_t M, const pc_build_opts& opts, 
             u64* set = sc.alloc<u64>((size_t)1 << log2cap);
             unsigned long long* counter = sc.alloc<unsigned long long>(1);
             if (!set || !counter) return pc_from_cuda(sc.err);
-            const double target = opts.occupancy > 0 ? opts.occupancy : 6.0;
+            const double target = opts.occupancy > 0 ? opts.occupancy : 12.0;
             double lo = h_floor, hi = (double)ext * 1.001;
             unsigned long long U = 0;
             PC_TRY(count_cells(xyz, M, o, (float)hi, set, log2cap, counter, s, &U));

@@ -388,31 +388,19 @@ __host__ __device__ float3 min_eigvec(float a00, float a01, float a02, float a11
     return make_float3(n.x * inv, n.y * inv, n.z * inv);
 }
 
-// Covariance of one neighbourhood row (Sec. III-C1, C_i of Eq. 19).
-// Two passes in binary32, both shifted by the first (nearest) neighbour p0
-// so the sums stay small: mean m of (p_j - p0), then the centred moments of
-// (p_j - p0) - m, divided by k.  Built with --fmad=false, so every + and *
-// below is rounded once and the fused and standalone kernels agree bit for
-// bit.  The row is nb[0], nb[st], ..., nb[(k-1) st].  `check`: validate
-// every index (pc_cov); otherwise a leading -1 marks an unanswered row.
-__device__ void cov_row(const Grid& g, const int32_t* nb, int st, int k, float eps, float* out,
-                        bool check) {
-    bool bad = nb[0] < 0;
-    if (check) {
-        bool oob = false;
-        for (int j = 0; j < k; ++j) oob |= (nb[j * st] < 0) || ((int64_t)nb[j * st] >= g.m);
-        if (oob) atomicOr(g.status, ST_BAD_INDEX);
-        bad = oob;
-    }
-    if (bad) {
-        const float nan = __int_as_float(0x7fc00000);
-        for (int e = 0; e < 6; ++e) out[e] = nan;
-        return;
-    }
-    const float4 p0 = __ldg(&g.xyz[nb[0]]);
+// Covariance of one neighbourhood (Sec. III-C1, C_i of Eq. 19) from its
+// points in rank order, get(j) for j = 0..k-1.  Two passes in binary32,
+// both shifted by the first (nearest) neighbour p0 so the sums stay small:
+// mean m of (p_j - p0), then the centred moments of (p_j - p0) - m, divided
+// by k.  Built with --fmad=false, so every + and * below is rounded once;
+// every caller runs this same code on the same values, so the fused kernel
+// and pc_cov agree bit for bit.
+template <typename G>
+__device__ __forceinline__ void cov_core(G&& get, int k, float eps, float* out) {
+    const float4 p0 = get(0);
     float sx = 0.0f, sy = 0.0f, sz = 0.0f;
     for (int j = 0; j < k; ++j) {
-        const float4 p = __ldg(&g.xyz[nb[j * st]]);
+        const float4 p = get(j);
         sx = sx + (p.x - p0.x);
         sy = sy + (p.y - p0.y);
         sz = sz + (p.z - p0.z);
@@ -421,7 +409,7 @@ __device__ void cov_row(const Grid& g, const int32_t* nb, int st, int k, float e
     const float mx = sx / fk, my = sy / fk, mz = sz / fk;
     float cxx = 0.0f, cxy = 0.0f, cxz = 0.0f, cyy = 0.0f, cyz = 0.0f, czz = 0.0f;
     for (int j = 0; j < k; ++j) {
-        const float4 p = __ldg(&g.xyz[nb[j * st]]);
+        const float4 p = get(j);
         const float dx = (p.x - p0.x) - mx;
         const float dy = (p.y - p0.y) - my;
         const float dz = (p.z - p0.z) - mz;
@@ -446,6 +434,30 @@ __device__ void cov_row(const Grid& g, const int32_t* nb, int st, int k, float e
     out[3] = 1.0f - f * n.y * n.y;
     out[4] = -f * n.y * n.z;
     out[5] = 1.0f - f * n.z * n.z;
+}
+
+__device__ __forceinline__ void nan_row(float* out) {
+    const float nan = __int_as_float(0x7fc00000);
+    for (int e = 0; e < 6; ++e) out[e] = nan;
+}
+
+// Covariance of the neighbourhood row nb[0], nb[st], ..., nb[(k-1) st]
+// (caller indices, read from the caller-order copy).  `check`: validate
+// every index (pc_cov); otherwise a leading -1 marks an unanswered row.
+__device__ void cov_row(const Grid& g, const int32_t* nb, int st, int k, float eps, float* out,
+                        bool check) {
+    bool bad = nb[0] < 0;
+    if (check) {
+        bool oob = false;
+        for (int j = 0; j < k; ++j) oob |= (nb[j * st] < 0) || ((int64_t)nb[j * st] >= g.m);
+        if (oob) atomicOr(g.status, ST_BAD_INDEX);
+        bad = oob;
+    }
+    if (bad) {
+        nan_row(out);
+        return;
+    }
+    cov_core([&](int j) { return __ldg(&g.xyz[nb[j * st]]); }, k, eps, out);
 }
 
 // ---------------------------------------------------------------- tiles
@@ -709,12 +721,18 @@ __device__ void lane_tile(const Grid& g, const float* __restrict__ q, int64_t n0
         amb = swapped;
     }
     if (m > 0) {
+        // rank-ordered positions, rewritten in place into the list's first k slots
+        uint32_t P[LANE_CAP];
+#pragma unroll
+        for (int r = 0; r < LANE_CAP; ++r)
+            if (r < k) P[r] = posl[(K[r] & 31u) * 32 + lane];
 #pragma unroll
         for (int r = 0; r < LANE_CAP; ++r)
             if (r < k) {
-                const u64 key = slot_key(g, posl, (int)(K[r] & 31u), lane, qx, qy, qz);
-                idx[n * k + r] = (int32_t)(uint32_t)key;
-                d2[n * k + r] = __uint_as_float((uint32_t)(key >> 32));
+                posl[r * 32 + lane] = P[r];
+                const float4 p = __ldg(&g.pts[P[r]]);
+                idx[n * k + r] = (int32_t)__float_as_uint(p.w);
+                d2[n * k + r] = sqdist_pinned(qx, qy, qz, p.x, p.y, p.z);
             }
     } else if (active && !finite) {
         for (int r = 0; r < k; ++r) {
@@ -746,7 +764,10 @@ __device__ void lane_tile(const Grid& g, const float* __restrict__ q, int64_t n0
     }
     if (COV && cov != nullptr) {
         __syncwarp();  // orders the idx rows written by other lanes
-        if (active) cov_row(g, idx + n * k, 1, k, a.eps, cov + 6 * n, false);
+        if (m > 0)  // neighbours straight from the cell-sorted copy, in rank order
+            cov_core([&](int j) { return __ldg(&g.pts[posl[j * 32 + lane]]); }, k, a.eps, cov + 6 * n);
+        else if (active)
+            cov_row(g, idx + n * k, 1, k, a.eps, cov + 6 * n, false);
     }
     __syncwarp();
 }

@@ -67,7 +67,7 @@ pc_status check_query_args(const pc_target_s* t, int64_t N, int k) {
 void default_tune(pc_tune* tu) {
     tu->tile = 32;
     tu->warps = 4;
-    tu->rho_scale = 1.0f;
+    tu->rho_scale = 0.9f;
 }
 
 pc_status read_and_clear_status(pc_target_s* t, cudaStream_t s) {
@@ -158,7 +158,7 @@ pc_status pc_from_cuda(cudaError_t e) {
 float pc_rho0(const pc_target_s* t, int k) {
     float r = (k >= 1 && k <= 64) ? t->rho_hint[k - 1] : 0.0f;
     if (!(r > 0.0f)) r = t->g.h;
-    const float sc = t->tune.rho_scale > 0 ? t->tune.rho_scale : 1.0f;
+    const float sc = t->tune.rho_scale > 0 ? t->tune.rho_scale : 0.9f;
     return r * sc;
 }
 
@@ -167,7 +167,7 @@ extern "C" {
 void pc_default_build_opts(pc_build_opts* o) {
     if (!o) return;
     o->cell_size = 0.0f;
-    o->occupancy = 6.0f;
+    o->occupancy = 12.0f;
     o->hash_load = 0.5f;
     o->max_box_cells = 4096;
     o->exhaustive = 1;
@@ -182,7 +182,7 @@ pc_status pc_build_target(const float* xyz_dev, int64_t M, const pc_build_opts* 
     pc_build_opts o;
     pc_default_build_opts(&o);
     if (opts) o = *opts;
-    if (o.occupancy <= 0) o.occupancy = 6.0f;
+    if (o.occupancy <= 0) o.occupancy = 12.0f;
     if (o.hash_load <= 0 || o.hash_load > 0.9f) o.hash_load = 0.5f;
     if (o.max_box_cells <= 0) o.max_box_cells = 4096;
     pc_target_s* t = new (std::nothrow) pc_target_s();
@@ -227,7 +227,7 @@ pc_status pc_set_tune(pc_target t, const pc_tune* tune) {
     t->tune = *tune;
     if (t->tune.tile <= 0) t->tune.tile = 32;
     if (t->tune.warps <= 0) t->tune.warps = 4;
-    if (t->tune.rho_scale <= 0) t->tune.rho_scale = 1.0f;
+    if (t->tune.rho_scale <= 0) t->tune.rho_scale = 0.9f;
     return PC_OK;
 }
 

@@ -49,7 +49,7 @@ def test_no_cuda_needed_for_strings_and_defaults(lib_path):
     assert pc.pc_version().startswith("pc ")
     assert pc.pc_status_string(pc.PC_ERR_K_GT_M) == "k larger than the target size"
     o = pc.pc_default_build_opts()
-    assert o.cell_size == 0 and o.occupancy == 6 and o.hash_load == 0.5 and o.max_box_cells == 4096 and o.exhaustive == 1
+    assert o.cell_size == 0 and o.occupancy == 12 and o.hash_load == 0.5 and o.max_box_cells == 4096 and o.exhaustive == 1
 
 
 def test_build_targets_sm_103a_only():
