@@ -190,6 +190,37 @@ PC_API pc_status pc_batch_plan(pc_target t, const pc_scan *scans, int n_scans, i
 PC_API pc_status pc_batch_run(pc_batch b, pc_stream s);
 PC_API void pc_batch_destroy(pc_batch b);
 
+/* Largest n_scans that pc_batch_run_noalloc accepts. */
+#define PC_NOALLOC_MAX_SCANS 256
+
+/* The batched search + covariance of pc_batch_plan/pc_batch_run in one call
+ * that allocates no memory at all.  The paper has no counterpart; this entry
+ * is for callers that may not allocate device memory once they are running:
+ * a real-time estimation loop that reserves its GPU memory at start-up and
+ * must not stall later (cudaMalloc and cudaFree can synchronise the whole
+ * device), or an application that hands out every device buffer from its
+ * own pool.  It calls no cudaMalloc, cudaFree or other allocating routine.
+ *
+ * Its scratch -- the scan table and the kernel's work counter -- lives in
+ * one file-scope device array sized for PC_NOALLOC_MAX_SCANS scans (about
+ * 12 KB), which every GPU that loads the library keeps until the process
+ * exits.  The caller still passes the target, and the inputs and outputs in
+ * `scans` (device pointers, as for pc_batch_plan).
+ *  - n_scans < 1 or > PC_NOALLOC_MAX_SCANS returns PC_ERR_INVALID_ARG and
+ *    launches nothing; other argument errors are those of pc_batch_plan.
+ *  - The first call on a device looks up the array's device address (once
+ *    per device, with that device current); make that first call before
+ *    any stream capture.
+ *  - Every call on a device uses the same array and it keeps the last
+ *    call's contents (the counter is cleared at the start of each call):
+ *    calls that overlap on the GPU -- on two streams, or from two host
+ *    threads -- race and corrupt each other's results.  Serialise them.
+ *  - Asynchronous on `s`; the scan table is copied from the caller's host
+ *    array before the call returns, so that array may be reused at once.
+ *    Results are identical to pc_knn_cov on each scan alone. */
+PC_API pc_status pc_batch_run_noalloc(pc_target t, const pc_scan *scans, int n_scans, int k,
+                                      float eps, pc_stream s);
+
 PC_API const char *pc_status_string(pc_status st);
 
 /* Library version string, e.g. "pc 0.1 sm_103a". */

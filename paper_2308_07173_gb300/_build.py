@@ -20,7 +20,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libpc.so")
 
-SOURCES = ["pc_api.cu", "grid_build.cu", "knn_cov.cu"]
+SOURCES = ["pc_api.cu", "grid_build.cu", "knn_cov.cu", "noalloc.cu"]
 HEADERS = ["pc_device.cuh", "pc_internal.h"]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

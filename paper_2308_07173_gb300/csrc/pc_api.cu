@@ -155,6 +155,10 @@ pc_status pc_from_cuda(cudaError_t e) {
     return PC_ERR_CUDA;
 }
 
+bool pc_target_is_live(const pc_target_s* t) { return t != nullptr && live(t); }
+
+bool pc_is_device_ptr(const void* p) { return is_device_ptr(p); }
+
 float pc_rho0(const pc_target_s* t, int k) {
     float r = (k >= 1 && k <= 64) ? t->rho_hint[k - 1] : 0.0f;
     if (!(r > 0.0f)) r = t->g.h;

@@ -84,3 +84,5 @@ int pc_knn_batch_blocks(int k, bool with_cov, int warps);
 // pc_api.cu
 float pc_rho0(const pc_target_s* t, int k);
 pc_status pc_from_cuda(cudaError_t e);
+bool pc_target_is_live(const pc_target_s* t);
+bool pc_is_device_ptr(const void* p);

@@ -28,6 +28,7 @@ PC_ERR_SEARCH_LIMIT = 6
 PC_ERR_BAD_POINTER = 7
 PC_ERR_BAD_INDEX = 8
 PC_ERR_DESTROYED = 9
+PC_NOALLOC_MAX_SCANS = 256
 
 _STATUS_NAMES = {
     0: "PC_OK",
@@ -114,6 +115,7 @@ SIGNATURES = {
     "pc_batch_plan": (_INT, [_VP, ctypes.POINTER(pc_scan), _INT, _INT, _F, ctypes.POINTER(_VP)]),
     "pc_batch_run": (_INT, [_VP, _VP]),
     "pc_batch_destroy": (None, [_VP]),
+    "pc_batch_run_noalloc": (_INT, [_VP, ctypes.POINTER(pc_scan), _INT, _INT, _F, _VP]),
     "pc_status_string": (ctypes.c_char_p, [_INT]),
     "pc_version": (ctypes.c_char_p, []),
 }
@@ -210,6 +212,11 @@ def pc_batch_plan(t, scans: Sequence[pc_scan], k: int, eps: float) -> int:
 
 def pc_batch_run(b, stream) -> int:
     return load().pc_batch_run(b, stream)
+
+
+def pc_batch_run_noalloc(t, scans: Sequence[pc_scan], k: int, eps: float, stream) -> int:
+    arr = (pc_scan * len(scans))(*scans)
+    return load().pc_batch_run_noalloc(t, arr, len(scans), k, eps, stream)
 
 
 def pc_batch_destroy(b) -> None:
