@@ -190,6 +190,22 @@ PC_API pc_status pc_batch_plan(pc_target t, const pc_scan *scans, int n_scans, i
 PC_API pc_status pc_batch_run(pc_batch b, pc_stream s);
 PC_API void pc_batch_destroy(pc_batch b);
 
+/* Bytes of device scratch pc_batch_run_scratch needs for n_scans scans. */
+PC_API size_t pc_batch_scratch_bytes(int n_scans);
+
+/* The batched form (same kernel and results as pc_batch_run) with scratch
+ * the caller owns: scratch_dev is device memory of at least
+ * pc_batch_scratch_bytes(n_scans) bytes, 256-byte aligned, used for the scan
+ * table and the work counter.  No allocation and no graph.  Calls with
+ * distinct scratch may run concurrently on different streams and overlap on
+ * the device -- the continuous-batching server launches each step this way.
+ * Asynchronous on `s`; the scan table is copied from `scans` before the call
+ * returns.  Errors: those of pc_batch_plan, PC_ERR_INVALID_ARG for a NULL,
+ * misaligned or too small scratch. */
+PC_API pc_status pc_batch_run_scratch(pc_target t, const pc_scan *scans, int n_scans, int k,
+                                      float eps, void *scratch_dev, size_t scratch_bytes,
+                                      pc_stream s);
+
 /* Largest n_scans that pc_batch_run_noalloc accepts. */
 #define PC_NOALLOC_MAX_SCANS 256
 

@@ -458,6 +458,63 @@ pc_status pc_batch_run(pc_batch b, pc_stream s) {
     return pc_from_cuda(cudaGraphLaunch(b->exec, st));
 }
 
+size_t pc_batch_scratch_bytes(int n_scans) {
+    if (n_scans < 1) return 0;
+    return 256 + sizeof(ScanDesc) * (size_t)n_scans;
+}
+
+pc_status pc_batch_run_scratch(pc_target t, const pc_scan* scans, int n_scans, int k, float eps,
+                               void* scratch_dev, size_t scratch_bytes, pc_stream s) {
+    pc_status r = check_target(t);
+    if (r != PC_OK) return r;
+    if (!scans || n_scans < 1 || k < 1 || k > 64 || !std::isfinite(eps)) return PC_ERR_INVALID_ARG;
+    if ((int64_t)k > t->g.m) return PC_ERR_K_GT_M;
+    if (!scratch_dev || (reinterpret_cast<uintptr_t>(scratch_dev) & 255u) ||
+        scratch_bytes < pc_batch_scratch_bytes(n_scans))
+        return PC_ERR_INVALID_ARG;
+    if (!is_device_ptr(scratch_dev)) return PC_ERR_BAD_POINTER;
+    bool any_cov = false;
+    for (int i = 0; i < n_scans; ++i) {
+        const pc_scan& sc = scans[i];
+        if (sc.n < 0) return PC_ERR_INVALID_ARG;
+        if (sc.n == 0) continue;
+        if (!sc.q_dev || !sc.idx_dev || !sc.d2_dev) return PC_ERR_INVALID_ARG;
+        if (!is_device_ptr(sc.q_dev) || !is_device_ptr(sc.idx_dev) || !is_device_ptr(sc.d2_dev))
+            return PC_ERR_BAD_POINTER;
+        if (sc.cov_dev) {
+            if (!is_device_ptr(sc.cov_dev)) return PC_ERR_BAD_POINTER;
+            any_cov = true;
+        }
+    }
+    DeviceGuard dg(t->device);
+    const int tile = std::min(std::max(t->tune.tile, 1), 32);
+    const int warps = std::min(std::max(t->tune.warps, 1), 8);
+    std::vector<ScanDesc> hs(n_scans);
+    int64_t tiles = 0;
+    for (int i = 0; i < n_scans; ++i) {
+        hs[i].q = scans[i].q_dev;
+        hs[i].n = scans[i].n;
+        hs[i].idx = scans[i].idx_dev;
+        hs[i].d2 = scans[i].d2_dev;
+        hs[i].cov = scans[i].cov_dev;
+        hs[i].tile0 = tiles;
+        tiles += (scans[i].n + tile - 1) / tile;
+    }
+    if (tiles == 0) return PC_OK;
+    cudaStream_t st = (cudaStream_t)s;
+    auto* base = static_cast<unsigned char*>(scratch_dev);
+    auto* counter = reinterpret_cast<unsigned long long*>(base);
+    auto* table = reinterpret_cast<ScanDesc*>(base + 256);
+    const int blocks = pc_knn_batch_blocks(k, any_cov, warps);
+    cudaError_t e = cudaMemcpyAsync(table, hs.data(), sizeof(ScanDesc) * n_scans,
+                                    cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), st);
+    if (e == cudaSuccess)
+        e = pc_launch_knn_batch(t, table, n_scans, tiles, tile, warps, blocks, k, eps, any_cov,
+                                pc_rho0(t, k), counter, st);
+    return pc_from_cuda(e);
+}
+
 void pc_batch_destroy(pc_batch b) {
     if (!b || !live(b)) return;
     untrack(b);

@@ -116,6 +116,8 @@ SIGNATURES = {
     "pc_batch_run": (_INT, [_VP, _VP]),
     "pc_batch_destroy": (None, [_VP]),
     "pc_batch_run_noalloc": (_INT, [_VP, ctypes.POINTER(pc_scan), _INT, _INT, _F, _VP]),
+    "pc_batch_scratch_bytes": (ctypes.c_size_t, [_INT]),
+    "pc_batch_run_scratch": (_INT, [_VP, ctypes.POINTER(pc_scan), _INT, _INT, _F, _VP, ctypes.c_size_t, _VP]),
     "pc_status_string": (ctypes.c_char_p, [_INT]),
     "pc_version": (ctypes.c_char_p, []),
 }
@@ -217,6 +219,16 @@ def pc_batch_run(b, stream) -> int:
 def pc_batch_run_noalloc(t, scans: Sequence[pc_scan], k: int, eps: float, stream) -> int:
     arr = (pc_scan * len(scans))(*scans)
     return load().pc_batch_run_noalloc(t, arr, len(scans), k, eps, stream)
+
+
+def pc_batch_scratch_bytes(n_scans: int) -> int:
+    return int(load().pc_batch_scratch_bytes(n_scans))
+
+
+def pc_batch_run_scratch(t, scans: Sequence[pc_scan], k: int, eps: float, scratch_dev: int,
+                         scratch_bytes: int, stream) -> int:
+    arr = (pc_scan * len(scans))(*scans)
+    return load().pc_batch_run_scratch(t, arr, len(scans), k, eps, scratch_dev, scratch_bytes, stream)
 
 
 def pc_batch_destroy(b) -> None:

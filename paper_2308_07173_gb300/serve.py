@@ -1,0 +1,231 @@
+"""Continuous-batching request loop for kNN + covariance over a resident map.
+
+Scans arrive from many simulated LiDARs (the paper's estimator runs one
+scan-match correction per scan, Sec. III-C3; here many sensors share one
+GPU).  The map's grid stays resident on the device.  The loop:
+
+* moves arrived requests to a pending queue (arrival times are replayed in
+  real time, optionally sped up);
+* admits pending requests while their device bytes (scan + idx + d2 + cov)
+  fit in the HBM budget, and a step slot is free;
+* launches each admitted group as ONE batched kernel (pc_batch_run_scratch)
+  on the slot's own stream: host-to-device copies, the persistent kernel and
+  device-to-host copies are queued on that stream, so a new step's copies
+  and kernel overlap the steps already on the GPU;
+* retires steps whose completion event has fired, frees their bytes and
+  slot, and stamps each request's completion time.
+
+Latency is completion minus arrival.  ``serve_per_scan`` is the baseline:
+one synchronous host-buffer call (pc_knn_cov_host) per scan in arrival
+order.  Both paths run the same exact kernels, so every result is the same
+alone and in the mix.
+"""
+from __future__ import annotations
+
+import time
+from collections import deque
+from dataclasses import dataclass, field
+from typing import List, Optional, Sequence
+
+import numpy as np
+
+from . import pc
+
+
+@dataclass
+class Request:
+    rid: int
+    t_arrival: float          # seconds from the start of the stream
+    points: np.ndarray        # [n,3] float32
+    t_sched: float = -1.0     # arrival time of this replay (t_arrival / speed)
+    t_admit: float = -1.0
+    t_done: float = -1.0
+    q_host: object = None     # pinned input copy
+    out_host: tuple = ()      # pinned idx, d2, cov
+    dev: tuple = ()           # device q, idx, d2, cov while in flight
+
+    @property
+    def n(self) -> int:
+        return int(self.points.shape[0])
+
+    @property
+    def latency(self) -> float:
+        return self.t_done - self.t_sched
+
+
+def latency_report(reqs: Sequence[Request], wall: float) -> dict:
+    lat = np.array([r.latency for r in reqs]) * 1e3
+    pts = sum(r.n for r in reqs)
+    return {
+        "scans": len(reqs),
+        "points": int(pts),
+        "p50_ms": float(np.percentile(lat, 50)),
+        "p99_ms": float(np.percentile(lat, 99)),
+        "mean_ms": float(lat.mean()),
+        "max_ms": float(lat.max()),
+        "wall_s": wall,
+        "throughput_pts_s": pts / wall if wall > 0 else float("nan"),
+    }
+
+
+def prepare(reqs: Sequence[Request]):
+    """Pinned host copies of every request's points (a sensor driver would
+    write into pinned buffers); done outside any timed region."""
+    import torch
+
+    for r in reqs:
+        r.q_host = torch.from_numpy(np.ascontiguousarray(r.points, dtype=np.float32)).pin_memory()
+        r.out_host = ()
+        r.t_admit = r.t_done = r.t_sched = -1.0
+
+
+def _pinned_outputs(n: int, k: int):
+    import torch
+
+    return (torch.empty((n, k), dtype=torch.int32, pin_memory=True),
+            torch.empty((n, k), dtype=torch.float32, pin_memory=True),
+            torch.empty((n, 6), dtype=torch.float32, pin_memory=True))
+
+
+@dataclass
+class _Step:
+    slot: int
+    reqs: List[Request]
+    done: object
+    nbytes: int
+
+
+class Server:
+    def __init__(self, target: "pc.Target", k: int, eps: float, hbm_budget: Optional[int] = None,
+                 max_step_scans: int = 32, slots: int = 3, keep_results: bool = False):
+        import torch
+
+        self.t = target
+        self.k = int(k)
+        self.eps = float(eps)
+        self.dev = target.device
+        if hbm_budget is None:
+            free, _ = torch.cuda.mem_get_info(self.dev)
+            hbm_budget = int(free * 0.5)
+        self.budget = int(hbm_budget)
+        self.max_step = int(max_step_scans)
+        self.streams = [torch.cuda.Stream(self.dev) for _ in range(slots)]
+        self.scratch_bytes = pc.pc_batch_scratch_bytes(self.max_step)
+        self.scratch = [torch.empty(self.scratch_bytes, dtype=torch.uint8, device=self.dev)
+                        for _ in range(slots)]
+        self.steps_launched = 0
+        self.keep = keep_results
+
+    def request_bytes(self, n: int) -> int:
+        return n * (12 + 8 * self.k + 24)
+
+    def _launch(self, slot: int, reqs: List[Request]) -> _Step:
+        import torch
+
+        s = self.streams[slot]
+        k = self.k
+        descs = []
+        with torch.cuda.stream(s):
+            for r in reqs:
+                q = r.q_host.to(self.dev, non_blocking=True)
+                idx = torch.empty((r.n, k), dtype=torch.int32, device=self.dev)
+                d2 = torch.empty((r.n, k), dtype=torch.float32, device=self.dev)
+                cov = torch.empty((r.n, 6), dtype=torch.float32, device=self.dev)
+                r.dev = (q, idx, d2, cov)
+                descs.append(pc.pc_scan(q.data_ptr(), r.n, idx.data_ptr(), d2.data_ptr(), cov.data_ptr()))
+            rc = pc.pc_batch_run_scratch(self.t.handle, descs, k, self.eps, self.scratch[slot].data_ptr(),
+                                         self.scratch_bytes, int(s.cuda_stream))
+            if rc != pc.PC_OK:
+                raise pc.PcError(rc, "pc_batch_run_scratch")
+            for r in reqs:
+                if not r.out_host:
+                    r.out_host = _pinned_outputs(r.n, k)
+                for host, devt in zip(r.out_host, r.dev[1:]):
+                    host.copy_(devt, non_blocking=True)
+            done = torch.cuda.Event()
+            done.record(s)
+        self.steps_launched += 1
+        return _Step(slot, reqs, done, sum(self.request_bytes(r.n) for r in reqs))
+
+    def serve(self, reqs: Sequence[Request], speed: float = 1.0) -> dict:
+        """Replay the arrivals (times divided by `speed`) and serve them."""
+        reqs = sorted(reqs, key=lambda r: r.t_arrival)
+        for r in reqs:
+            r.t_sched = r.t_arrival / speed
+        self.steps_launched = 0
+        pending: deque = deque()
+        inflight: List[_Step] = []
+        free_slots = list(range(len(self.streams)))
+        used = 0
+        nxt = 0
+        done = 0
+        t0 = time.perf_counter()
+        while done < len(reqs):
+            now = time.perf_counter() - t0
+            while nxt < len(reqs) and reqs[nxt].t_sched <= now:
+                pending.append(reqs[nxt])
+                nxt += 1
+            for st in list(inflight):
+                if st.done.query():
+                    tdone = time.perf_counter() - t0
+                    for r in st.reqs:
+                        r.t_done = tdone
+                        r.dev = ()
+                        if not self.keep:
+                            r.out_host = ()
+                    used -= st.nbytes
+                    free_slots.append(st.slot)
+                    inflight.remove(st)
+                    done += len(st.reqs)
+            if pending and free_slots:
+                batch = []
+                while pending and len(batch) < self.max_step:
+                    b = self.request_bytes(pending[0].n)
+                    if used + b > self.budget and (batch or inflight):
+                        break
+                    r = pending.popleft()
+                    r.t_admit = now
+                    used += b
+                    batch.append(r)
+                if batch:
+                    inflight.append(self._launch(free_slots.pop(0), batch))
+                    continue
+            if not pending and not inflight and nxt < len(reqs):
+                wait = reqs[nxt].t_sched - (time.perf_counter() - t0)
+                if wait > 2e-4:
+                    time.sleep(wait - 1e-4)
+        wall = max(r.t_done for r in reqs) - reqs[0].t_sched
+        out = latency_report(reqs, wall)
+        out["steps"] = self.steps_launched
+        out["mean_scans_per_step"] = len(reqs) / max(1, self.steps_launched)
+        return out
+
+
+def serve_per_scan(target: "pc.Target", k: int, eps: float, reqs: Sequence[Request], speed: float = 1.0,
+                   stream=None, keep_results: bool = False) -> dict:
+    """Baseline: each scan in arrival order through one synchronous
+    host-buffer call (copies in, kernel, copies out)."""
+    import torch
+
+    reqs = sorted(reqs, key=lambda r: r.t_arrival)
+    for r in reqs:
+        r.t_sched = r.t_arrival / speed
+    stream = stream or torch.cuda.Stream(target.device)
+    t0 = time.perf_counter()
+    for r in reqs:
+        wait = r.t_sched - (time.perf_counter() - t0)
+        if wait > 2e-4:
+            time.sleep(wait - 1e-4)
+        while time.perf_counter() - t0 < r.t_sched:
+            pass
+        r.t_admit = time.perf_counter() - t0
+        out = r.out_host if r.out_host else _pinned_outputs(r.n, k)
+        target.knn_cov_host(r.q_host, k, eps, out=out, stream=stream)
+        r.t_done = time.perf_counter() - t0
+        r.out_host = out if keep_results else ()
+    wall = max(r.t_done for r in reqs) - reqs[0].t_sched
+    return latency_report(reqs, wall)
+
+
+def requests_from_arrivals(arrivals) -> List[Request]:
+    return [Request(i, a.t, a.points) for i, a in enumerate(arrivals)]

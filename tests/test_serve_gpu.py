@@ -1,0 +1,80 @@
+"""Served form: continuous batching gives every scan the same neighbours,
+distances and covariances it gets alone, and so does the per-scan baseline;
+the caller-scratch batched entry matches too."""
+import numpy as np
+import pytest
+
+from paper_2308_07173_gb300 import serve
+from paper_2308_07173_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def small_world(gpu_lib):
+    tr = W.oval_1500()
+    m = tr.sample_map(400_000, seed=31)
+    t = gpu_lib.Target(torch.from_numpy(m).cuda())
+    arr = W.arrival_stream(duration=0.25, vehicles=2, sensors=3, lo=3000, hi=30000, pool=6, seed=32)
+    yield t, arr
+    t.close()
+
+
+def _alone(t, pts, k, eps):
+    i, d, c = t.knn_cov(torch.from_numpy(pts).cuda(), k, eps)
+    torch.cuda.synchronize()
+    return i.cpu(), d.cpu(), c.cpu()
+
+
+def _same(a, b):
+    return (torch.equal(a[0], b[0]) and torch.equal(a[1].view(torch.int32), b[1].view(torch.int32))
+            and torch.equal(a[2].view(torch.int32), b[2].view(torch.int32)))
+
+
+@pytest.mark.parametrize("speed", [1.0, 1e6])
+def test_served_results_equal_alone(small_world, gpu_lib, speed):
+    t, arr = small_world
+    k, eps = 20, 1e-3
+    reqs = serve.requests_from_arrivals(arr)
+    assert len(reqs) > 10
+    serve.prepare(reqs)
+    srv = serve.Server(t, k, eps, hbm_budget=64 << 20, max_step_scans=4, slots=2, keep_results=True)
+    rep = srv.serve(reqs, speed=speed)
+    assert rep["scans"] == len(reqs) and rep["p99_ms"] >= rep["p50_ms"] > 0
+    if speed > 1:
+        assert rep["mean_scans_per_step"] > 1.0  # requests really were batched
+    for r in reqs:
+        assert r.t_done >= r.t_admit >= r.t_sched
+        assert _same(r.out_host, _alone(t, r.points, k, eps))
+    assert t.sync_status() == gpu_lib.PC_OK
+
+
+def test_per_scan_baseline_equal_alone(small_world, gpu_lib):
+    t, arr = small_world
+    k, eps = 20, 1e-3
+    reqs = serve.requests_from_arrivals(arr[:8])
+    serve.prepare(reqs)
+    rep = serve.serve_per_scan(t, k, eps, reqs, speed=1e6, keep_results=True)
+    assert rep["scans"] == 8
+    for r in reqs:
+        assert _same(r.out_host, _alone(t, r.points, k, eps))
+
+
+def test_batch_scratch_entry_checks_scratch(small_world, gpu_lib):
+    t, arr = small_world
+    pts = torch.from_numpy(arr[0].points).cuda()
+    n, k = pts.shape[0], 12
+    idx = torch.empty((n, k), dtype=torch.int32, device="cuda")
+    d2 = torch.empty((n, k), dtype=torch.float32, device="cuda")
+    descs = [gpu_lib.pc_scan(pts.data_ptr(), n, idx.data_ptr(), d2.data_ptr(), None)]
+    need = gpu_lib.pc_batch_scratch_bytes(1)
+    scratch = torch.empty(need, dtype=torch.uint8, device="cuda")
+    assert gpu_lib.pc_batch_run_scratch(t.handle, descs, k, -1.0, scratch.data_ptr(), need - 1, 0) \
+        == gpu_lib.PC_ERR_INVALID_ARG
+    assert gpu_lib.pc_batch_run_scratch(t.handle, descs, k, -1.0, scratch.data_ptr() + 8, need, 0) \
+        == gpu_lib.PC_ERR_INVALID_ARG
+    assert gpu_lib.pc_batch_run_scratch(t.handle, descs, k, -1.0, scratch.data_ptr(), need, 0) == gpu_lib.PC_OK
+    ri, rd = t.knn(pts, k)
+    torch.cuda.synchronize()
+    assert torch.equal(ri, idx) and torch.equal(rd.view(torch.int32), d2.view(torch.int32))
