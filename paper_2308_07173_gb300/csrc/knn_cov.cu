@@ -470,9 +470,12 @@ struct TileArgs {
 // Per-warp shared memory: 64 staged survivor keys of the warp-cooperative
 // search, then the lane path's survivor lists: 32 slots x 32 lanes of
 // positions into pts ([slot][lane], so a slot is one 128-byte row).
-constexpr int LANE_CAP = 32;  // survivors the lane path can sort
-__host__ __device__ __forceinline__ size_t warp_smem_bytes() {
-    return 64 * sizeof(u64) + (size_t)LANE_CAP * 32 * sizeof(uint32_t);
+// Search modes: 0 = lane path with room for 32 survivors (k <= 24),
+// 1 = lane path with room for 64 (k <= 32), 2 = warp path only (k > 32).
+__host__ __device__ __forceinline__ int lane_cap(int mode) { return mode == 0 ? 32 : mode == 1 ? 64 : 0; }
+__host__ __device__ __forceinline__ int search_mode(int k) { return k <= 24 ? 0 : (k <= 32 ? 1 : 2); }
+__host__ __device__ __forceinline__ size_t warp_smem_bytes(int mode) {
+    return 64 * sizeof(u64) + (size_t)lane_cap(mode) * 32 * sizeof(uint32_t);
 }
 
 __device__ __forceinline__ void cas32(uint32_t& a, uint32_t& b) {
@@ -482,8 +485,8 @@ __device__ __forceinline__ void cas32(uint32_t& a, uint32_t& b) {
 }
 
 // Bitonic sort network over the first NN registers, ascending.
-template <int NN>
-__device__ __forceinline__ void sort_regs(uint32_t (&K)[LANE_CAP]) {
+template <int NN, int CAP>
+__device__ __forceinline__ void sort_regs(uint32_t (&K)[CAP]) {
 #pragma unroll
     for (int size = 2; size <= NN; size <<= 1)
 #pragma unroll
@@ -599,7 +602,7 @@ __device__ __forceinline__ u64 slot_key(const Grid& g, const uint32_t* posl, int
 // index) order by bubble passes on the full keys.  Lanes whose query needs
 // a wider radius, more than 32 survivors or a bigger box are finished by
 // the warp-cooperative search, one query at a time.
-template <bool COV>
+template <int CAP, bool COV>
 __device__ void lane_tile(const Grid& g, const float* __restrict__ q, int64_t n0, int cnt,
                           const TileArgs& a, float rho0, int32_t* __restrict__ idx,
                           float* __restrict__ d2, float* __restrict__ cov, u64* pend,
@@ -666,7 +669,7 @@ __device__ void lane_tile(const Grid& g, const float* __restrict__ q, int64_t n0
 #pragma unroll
             for (int j = 0; j < NRAD; ++j)
                 if (j == js) { cj = c[j]; tj = t[j]; }
-            if (js < 0 || cj > LANE_CAP) {
+            if (js < 0 || cj > CAP) {
                 fallback = true;
             } else {
                 m = cj;
@@ -678,7 +681,7 @@ __device__ void lane_tile(const Grid& g, const float* __restrict__ q, int64_t n0
         int w = 0;
         auto collect = [&](uint32_t pos, const float4 p) {
             const float d = sqdist_pinned(qx, qy, qz, p.x, p.y, p.z);
-            if (d <= thr && w < LANE_CAP) {
+            if (d <= thr && w < CAP) {
                 posl[w * 32 + lane] = pos;
                 ++w;
             }
@@ -687,29 +690,31 @@ __device__ void lane_tile(const Grid& g, const float* __restrict__ q, int64_t n0
         else for_box_points(g, qx, qy, qz, lx, hx, ly, hy, lz, hz, eta, thr, collect);
     }
     __syncwarp();
-    uint32_t K[LANE_CAP];
+    uint32_t K[CAP];
 #pragma unroll
-    for (int s = 0; s < LANE_CAP; ++s) {
+    for (int s = 0; s < CAP; ++s) {
         uint32_t key = 0xffffffffu;
         if (s < m) {
             const float4 p = __ldg(&g.pts[posl[s * 32 + lane]]);
             const float d = sqdist_pinned(qx, qy, qz, p.x, p.y, p.z);
-            key = ((__float_as_uint(d) << 1) & ~31u) | (uint32_t)s;
+            key = ((__float_as_uint(d) << 1) & ~(uint32_t)(CAP - 1)) | (uint32_t)s;
         }
         K[s] = key;
     }
-    if (__reduce_max_sync(FULL, (unsigned)m) <= 16u) sort_regs<16>(K);
-    else sort_regs<LANE_CAP>(K);
+    const unsigned mmax = __reduce_max_sync(FULL, (unsigned)m);
+    if (mmax <= 16u) sort_regs<16>(K);
+    else if (CAP == 32 || mmax <= 32u) sort_regs<32>(K);
+    else sort_regs<CAP>(K);
     bool amb = false;
 #pragma unroll
-    for (int r = 0; r + 1 < LANE_CAP; ++r) amb |= (r + 1 < m) && ((K[r] ^ K[r + 1]) < 32u);
-    for (int pass = 0; amb && pass < LANE_CAP; ++pass) {
+    for (int r = 0; r + 1 < CAP; ++r) amb |= (r + 1 < m) && ((K[r] ^ K[r + 1]) < (uint32_t)CAP);
+    for (int pass = 0; amb && pass < CAP; ++pass) {
         bool swapped = false;
 #pragma unroll
-        for (int r = 0; r + 1 < LANE_CAP; ++r) {
-            if (r + 1 < m && ((K[r] ^ K[r + 1]) < 32u)) {
-                const u64 ka = slot_key(g, posl, (int)(K[r] & 31u), lane, qx, qy, qz);
-                const u64 kb = slot_key(g, posl, (int)(K[r + 1] & 31u), lane, qx, qy, qz);
+        for (int r = 0; r + 1 < CAP; ++r) {
+            if (r + 1 < m && ((K[r] ^ K[r + 1]) < (uint32_t)CAP)) {
+                const u64 ka = slot_key(g, posl, (int)(K[r] & (CAP - 1)), lane, qx, qy, qz);
+                const u64 kb = slot_key(g, posl, (int)(K[r + 1] & (CAP - 1)), lane, qx, qy, qz);
                 if (kb < ka) {
                     const uint32_t tmp = K[r];
                     K[r] = K[r + 1];
@@ -722,12 +727,12 @@ __device__ void lane_tile(const Grid& g, const float* __restrict__ q, int64_t n0
     }
     if (m > 0) {
         // rank-ordered positions, rewritten in place into the list's first k slots
-        uint32_t P[LANE_CAP];
+        uint32_t P[32];
 #pragma unroll
-        for (int r = 0; r < LANE_CAP; ++r)
-            if (r < k) P[r] = posl[(K[r] & 31u) * 32 + lane];
+        for (int r = 0; r < 32; ++r)
+            if (r < k) P[r] = posl[(K[r] & (CAP - 1)) * 32 + lane];
 #pragma unroll
-        for (int r = 0; r < LANE_CAP; ++r)
+        for (int r = 0; r < 32; ++r)
             if (r < k) {
                 posl[r * 32 + lane] = P[r];
                 const float4 p = __ldg(&g.pts[P[r]]);
@@ -815,7 +820,7 @@ __device__ void warp_tile(const Grid& g, const float* __restrict__ q, int64_t n0
     }
 }
 
-template <int SLOTS, bool COV>
+template <int MODE, bool COV>
 __device__ __forceinline__ void process_tile(const Grid& g, const float* __restrict__ q, int64_t n0,
                                              int cnt, const TileArgs& a, float rho0,
                                              int32_t* __restrict__ idx, float* __restrict__ d2,
@@ -823,13 +828,15 @@ __device__ __forceinline__ void process_tile(const Grid& g, const float* __restr
                                              int lane) {
     u64* pend = reinterpret_cast<u64*>(wsmem);
     uint32_t* posl = reinterpret_cast<uint32_t*>(wsmem + 64 * sizeof(u64));
-    if (SLOTS == 1)
-        lane_tile<COV>(g, q, n0, cnt, a, rho0, idx, d2, cov, pend, posl, lane);
+    if (MODE == 0)
+        lane_tile<32, COV>(g, q, n0, cnt, a, rho0, idx, d2, cov, pend, posl, lane);
+    else if (MODE == 1)
+        lane_tile<64, COV>(g, q, n0, cnt, a, rho0, idx, d2, cov, pend, posl, lane);
     else
         warp_tile<COV>(g, q, n0, cnt, a, rho0, idx, d2, cov, pend, lane);
 }
 
-template <int SLOTS, bool COV>
+template <int MODE, bool COV>
 __global__ void __launch_bounds__(256, 2) k_knn(Grid g, const float* __restrict__ q, int64_t N,
                                              int tile, TileArgs a, float rho0,
                                              int32_t* __restrict__ idx, float* __restrict__ d2,
@@ -841,20 +848,20 @@ __global__ void __launch_bounds__(256, 2) k_knn(Grid g, const float* __restrict_
     const int64_t n0 = t * tile;
     if (n0 >= N) return;
     const int cnt = (int)min((int64_t)tile, N - n0);
-    process_tile<SLOTS, COV>(g, q, n0, cnt, a, rho0, idx, d2, cov,
-                             smem + (size_t)warp * warp_smem_bytes(), lane);
+    process_tile<MODE, COV>(g, q, n0, cnt, a, rho0, idx, d2, cov,
+                            smem + (size_t)warp * warp_smem_bytes(MODE), lane);
 }
 
 // Batched form: one persistent launch; warps pull (scan, tile) items from a
 // device counter over the scans' prefix-summed tile table.
-template <int SLOTS, bool COV>
+template <int MODE, bool COV>
 __global__ void __launch_bounds__(256, 2) k_knn_batch(Grid g, const ScanDesc* __restrict__ scans,
                                                    int nscans, int64_t total_tiles, int tile,
                                                    TileArgs a, float rho0,
                                                    unsigned long long* counter) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    unsigned char* wsmem = smem + (size_t)warp * warp_smem_bytes();
+    unsigned char* wsmem = smem + (size_t)warp * warp_smem_bytes(MODE);
     for (;;) {
         unsigned long long item = 0;
         if (lane == 0) item = atomicAdd(counter, 1ull);
@@ -868,7 +875,7 @@ __global__ void __launch_bounds__(256, 2) k_knn_batch(Grid g, const ScanDesc* __
         const ScanDesc sd = scans[lo];
         const int64_t n0 = ((int64_t)item - sd.tile0) * tile;
         const int cnt = (int)min((int64_t)tile, sd.n - n0);
-        process_tile<SLOTS, COV>(g, sd.q, n0, cnt, a, rho0, sd.idx, sd.d2, sd.cov, wsmem, lane);
+        process_tile<MODE, COV>(g, sd.q, n0, cnt, a, rho0, sd.idx, sd.d2, sd.cov, wsmem, lane);
     }
 }
 
@@ -895,10 +902,14 @@ cudaError_t ensure_attrs() {
     const unsigned bit = 1u << (dev & 31);
     std::lock_guard<std::mutex> lk(g_attr_mu);
     if (g_attr_done & bit) return cudaSuccess;
+    if ((e = allow_smem(k_knn<0, true>)) != cudaSuccess) return e;
+    if ((e = allow_smem(k_knn<0, false>)) != cudaSuccess) return e;
     if ((e = allow_smem(k_knn<1, true>)) != cudaSuccess) return e;
     if ((e = allow_smem(k_knn<1, false>)) != cudaSuccess) return e;
     if ((e = allow_smem(k_knn<2, true>)) != cudaSuccess) return e;
     if ((e = allow_smem(k_knn<2, false>)) != cudaSuccess) return e;
+    if ((e = allow_smem(k_knn_batch<0, true>)) != cudaSuccess) return e;
+    if ((e = allow_smem(k_knn_batch<0, false>)) != cudaSuccess) return e;
     if ((e = allow_smem(k_knn_batch<1, true>)) != cudaSuccess) return e;
     if ((e = allow_smem(k_knn_batch<1, false>)) != cudaSuccess) return e;
     if ((e = allow_smem(k_knn_batch<2, true>)) != cudaSuccess) return e;
@@ -913,33 +924,46 @@ int clamp_warps(int w) { return w <= 0 ? 4 : (w > 8 ? 8 : w); }
 }  // namespace
 
 // ---------------------------------------------------------------- host side
+namespace {
+
+// Calls f(kernel) with the search kernel for (mode, with_cov).
+template <bool BATCH, typename F>
+cudaError_t with_kernel(int mode, bool with_cov, F&& f) {
+#define PC_PICK(M, C) (BATCH ? (void*)k_knn_batch<M, C> : (void*)k_knn<M, C>)
+    void* kern = nullptr;
+    switch (mode * 2 + (with_cov ? 1 : 0)) {
+        case 0: kern = PC_PICK(0, false); break;
+        case 1: kern = PC_PICK(0, true); break;
+        case 2: kern = PC_PICK(1, false); break;
+        case 3: kern = PC_PICK(1, true); break;
+        case 4: kern = PC_PICK(2, false); break;
+        default: kern = PC_PICK(2, true); break;
+    }
+#undef PC_PICK
+    return f(kern);
+}
+
+}  // namespace
+
 cudaError_t pc_launch_knn(const pc_target_s* t, const float* q, int64_t N, int k, float eps,
                           int32_t* idx, float* d2, float* cov, float rho0, cudaStream_t s) {
     if (N == 0) return cudaSuccess;
-    const int tile = clamp_tile(t->tune.tile);
-    const int warps = clamp_warps(t->tune.warps);
-    TileArgs a{k, eps, t->tune.rho_scale > 0 ? t->tune.rho_scale : 1.15f};
-    const bool with_cov = cov != nullptr;
-    const size_t smem = (size_t)warps * warp_smem_bytes();
-    const int64_t tiles = (N + tile - 1) / tile;
-    const int64_t blocks = (tiles + warps - 1) / warps;
-    const dim3 grid((unsigned)blocks), block(warps * 32);
     cudaError_t e = ensure_attrs();
     if (e != cudaSuccess) return e;
-    if (k <= 32) {
-        if (with_cov) {
-            k_knn<1, true><<<grid, block, smem, s>>>(t->g, q, N, tile, a, rho0, idx, d2, cov);
-        } else {
-            k_knn<1, false><<<grid, block, smem, s>>>(t->g, q, N, tile, a, rho0, idx, d2, nullptr);
-        }
-    } else {
-        if (with_cov) {
-            k_knn<2, true><<<grid, block, smem, s>>>(t->g, q, N, tile, a, rho0, idx, d2, cov);
-        } else {
-            k_knn<2, false><<<grid, block, smem, s>>>(t->g, q, N, tile, a, rho0, idx, d2, nullptr);
-        }
-    }
-    return cudaGetLastError();
+    const int tile = clamp_tile(t->tune.tile);
+    const int warps = clamp_warps(t->tune.warps);
+    TileArgs a{k, eps, t->tune.rho_scale > 0 ? t->tune.rho_scale : 0.9f};
+    const bool with_cov = cov != nullptr;
+    const int mode = search_mode(k);
+    const size_t smem = (size_t)warps * warp_smem_bytes(mode);
+    const int64_t tiles = (N + tile - 1) / tile;
+    const int64_t blocks = (tiles + warps - 1) / warps;
+    Grid g = t->g;
+    float* covp = with_cov ? cov : nullptr;
+    void* args[] = {&g, (void*)&q, (void*)&N, (void*)&tile, &a, &rho0, &idx, &d2, &covp};
+    return with_kernel<false>(mode, with_cov, [&](void* kern) {
+        return cudaLaunchKernel(kern, dim3((unsigned)blocks), dim3(warps * 32), args, smem, s);
+    });
 }
 
 cudaError_t pc_launch_cov(const pc_target_s* t, const int32_t* idx, int64_t N, int k, float eps,
@@ -955,51 +979,28 @@ cudaError_t pc_launch_knn_batch(const pc_target_s* t, const ScanDesc* scans_dev,
                                 int64_t total_tiles, int tile, int warps, int blocks, int k,
                                 float eps, bool with_cov, float rho0,
                                 unsigned long long* counter, cudaStream_t s) {
-    TileArgs a{k, eps, t->tune.rho_scale > 0 ? t->tune.rho_scale : 1.15f};
-    const size_t smem = (size_t)warps * warp_smem_bytes();
-    const dim3 grid((unsigned)blocks), block(warps * 32);
-    if (k <= 32) {
-        if (with_cov) {
-            k_knn_batch<1, true><<<grid, block, smem, s>>>(t->g, scans_dev, nscans, total_tiles,
-                                                         tile, a, rho0, counter);
-        } else {
-            k_knn_batch<1, false><<<grid, block, smem, s>>>(t->g, scans_dev, nscans, total_tiles,
-                                                          tile, a, rho0, counter);
-        }
-    } else {
-        if (with_cov) {
-            k_knn_batch<2, true><<<grid, block, smem, s>>>(t->g, scans_dev, nscans, total_tiles,
-                                                         tile, a, rho0, counter);
-        } else {
-            k_knn_batch<2, false><<<grid, block, smem, s>>>(t->g, scans_dev, nscans, total_tiles,
-                                                          tile, a, rho0, counter);
-        }
-    }
-    return cudaGetLastError();
+    TileArgs a{k, eps, t->tune.rho_scale > 0 ? t->tune.rho_scale : 0.9f};
+    const int mode = search_mode(k);
+    const size_t smem = (size_t)warps * warp_smem_bytes(mode);
+    Grid g = t->g;
+    void* args[] = {&g, (void*)&scans_dev, &nscans, &total_tiles, &tile, &a, &rho0, &counter};
+    return with_kernel<true>(mode, with_cov, [&](void* kern) {
+        return cudaLaunchKernel(kern, dim3((unsigned)blocks), dim3(warps * 32), args, smem, s);
+    });
 }
 
-size_t pc_knn_smem_per_warp(int k, bool with_cov) { return warp_smem_bytes(); }
+size_t pc_knn_smem_per_warp(int k, bool) { return warp_smem_bytes(search_mode(k)); }
 
 int pc_knn_batch_blocks(int k, bool with_cov, int warps) {
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const size_t smem = (size_t)warps * warp_smem_bytes();
-    cudaError_t e = ensure_attrs();
-    if (e != cudaSuccess) return sms;
-    if (k <= 32) {
-        if (with_cov) {
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_knn_batch<1, true>, warps * 32, smem);
-        } else {
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_knn_batch<1, false>, warps * 32, smem);
-        }
-    } else {
-        if (with_cov) {
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_knn_batch<2, true>, warps * 32, smem);
-        } else {
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_knn_batch<2, false>, warps * 32, smem);
-        }
-    }
+    if (ensure_attrs() != cudaSuccess) return sms;
+    const int mode = search_mode(k);
+    const size_t smem = (size_t)warps * warp_smem_bytes(mode);
+    const cudaError_t e = with_kernel<true>(mode, with_cov, [&](void* kern) {
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, warps * 32, smem);
+    });
     if (e != cudaSuccess || per_sm < 1) per_sm = 1;
     return sms * per_sm;
 }

@@ -90,7 +90,7 @@ def test_fused_equals_separate_calls(c1, gpu_lib):
 
 
 @pytest.mark.parametrize("n", [1, 31, 33, 1000])
-@pytest.mark.parametrize("k", [1, 7, 32, 33, 64])
+@pytest.mark.parametrize("k", [1, 7, 24, 25, 32, 33, 64])
 def test_ragged_sizes_and_k(c1, gpu_lib, n, k):
     p, t = c1
     g = np.random.default_rng(n * 100 + k)
