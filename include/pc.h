@@ -84,8 +84,10 @@ typedef struct {
                           <= 0: 32 */
     int warps;         /* warps per block, 1..8; <= 0: 4 */
     float rho_scale;   /* scales the target's calibrated k-th-neighbour radius that the
-                          search starts from (k <= 32: trial radii 0.7..1.75 x it);
+                          search starts from (k <= 32: trial radii 0.75..1.46 x it);
                           <= 0: 0.9 */
+    int order;         /* 0: issue query tiles last-first (a ring-by-ring LiDAR scan ends
+                          with its slowest, farthest rings); 1: first-first */
 } pc_tune;
 
 /* What the built target looks like (for reporting and tuning). */

@@ -465,6 +465,7 @@ struct TileArgs {
     int k;
     float eps;
     float rho_scale;
+    int last_first;  // issue tiles from the end of the query array
 };
 
 // Per-warp shared memory: 64 staged survivor keys of the warp-cooperative
@@ -622,58 +623,75 @@ __device__ void lane_tile(const Grid& g, const float* __restrict__ q, int64_t n0
     float thr = -1.0f;
     int lx = 0, hx = -1, ly = 0, hy = -1, lz = 0, hz = -1;
     float eta = 0.0f;
-    if (finite) {
-        const float rmax = rho0 * rad_mul(NRAD - 1);
-        const int ulx = cell_of(__fsub_rn(qx, rmax), g.ox, g.inv_h);
-        const int uhx = cell_of(__fadd_rn(qx, rmax), g.ox, g.inv_h);
-        const int uly = cell_of(__fsub_rn(qy, rmax), g.oy, g.inv_h);
-        const int uhy = cell_of(__fadd_rn(qy, rmax), g.oy, g.inv_h);
-        const int ulz = cell_of(__fsub_rn(qz, rmax), g.oz, g.inv_h);
-        const int uhz = cell_of(__fadd_rn(qz, rmax), g.oz, g.inv_h);
-        const float tau = certified_tau(g, qx, qy, qz, ulx, uhx, uly, uhy, ulz, uhz);
-        {
-            const int cm = max(max(max(abs(ulx), abs(uhx + 1)), max(abs(uly), abs(uhy + 1))),
-                               max(abs(ulz), abs(uhz + 1)));
-            const float qm = fmaxf(fabsf(qx), fmaxf(fabsf(qy), fabsf(qz)));
-            eta = 0x1p-20f * (g.coord_scale + qm + (float)cm * g.h);
-        }
-        lx = max(ulx, 0); hx = min(uhx, g.dimx - 1);
-        ly = max(uly, 0); hy = min(uhy, g.dimy - 1);
-        lz = max(ulz, 0); hz = min(uhz, g.dimz - 1);
-        const int64_t ncl = (int64_t)max(hx - lx + 1, 0) * max(hy - ly + 1, 0) * max(hz - lz + 1, 0);
-        const int64_t nrows = (int64_t)max(hy - ly + 1, 0) * max(hz - lz + 1, 0);
-        if (tau < 0.0f || ncl > 4096 || nrows > 256 || (!g.occ && ncl > 256)) {
-            fallback = true;
-        } else {
-            float t[NRAD];
-            int c[NRAD];
-#pragma unroll
-            for (int j = 0; j < NRAD; ++j) {
-                const float r = rho0 * rad_mul(j);
-                t[j] = fminf(r * r, tau);
-                c[j] = 0;
+    // Up to two lane-parallel attempts: a lane whose largest trial radius
+    // held fewer than k points retries with the radii x1.8, one whose
+    // smallest held more than CAP retries with them x0.7; only lanes that
+    // still fail go to the warp search.
+    float rho = rho0;
+    bool todo = finite;
+    for (int attempt = 0; attempt < 2 && __any_sync(FULL, todo); ++attempt) {
+        if (todo) {
+            todo = false;
+            const float rmax = rho * rad_mul(NRAD - 1);
+            const int ulx = cell_of(__fsub_rn(qx, rmax), g.ox, g.inv_h);
+            const int uhx = cell_of(__fadd_rn(qx, rmax), g.ox, g.inv_h);
+            const int uly = cell_of(__fsub_rn(qy, rmax), g.oy, g.inv_h);
+            const int uhy = cell_of(__fadd_rn(qy, rmax), g.oy, g.inv_h);
+            const int ulz = cell_of(__fsub_rn(qz, rmax), g.oz, g.inv_h);
+            const int uhz = cell_of(__fadd_rn(qz, rmax), g.oz, g.inv_h);
+            const float tau = certified_tau(g, qx, qy, qz, ulx, uhx, uly, uhy, ulz, uhz);
+            {
+                const int cm = max(max(max(abs(ulx), abs(uhx + 1)), max(abs(uly), abs(uhy + 1))),
+                                   max(abs(ulz), abs(uhz + 1)));
+                const float qm = fmaxf(fabsf(qx), fmaxf(fabsf(qy), fabsf(qz)));
+                eta = 0x1p-20f * (g.coord_scale + qm + (float)cm * g.h);
             }
-            auto count = [&](uint32_t, const float4 p) {
-                const float d = sqdist_pinned(qx, qy, qz, p.x, p.y, p.z);
-#pragma unroll
-                for (int j = 0; j < NRAD; ++j) c[j] += d <= t[j] ? 1 : 0;
-            };
-            if (g.occ) for_rows(g, qx, qy, qz, lx, hx, ly, hy, lz, hz, eta, t[NRAD - 1], count);
-            else for_box_points(g, qx, qy, qz, lx, hx, ly, hy, lz, hz, eta, t[NRAD - 1], count);
-            int js = -1;
-#pragma unroll
-            for (int j = NRAD - 1; j >= 0; --j)
-                if (c[j] >= k) js = j;
-            int cj = 0;
-            float tj = -1.0f;
-#pragma unroll
-            for (int j = 0; j < NRAD; ++j)
-                if (j == js) { cj = c[j]; tj = t[j]; }
-            if (js < 0 || cj > CAP) {
+            lx = max(ulx, 0); hx = min(uhx, g.dimx - 1);
+            ly = max(uly, 0); hy = min(uhy, g.dimy - 1);
+            lz = max(ulz, 0); hz = min(uhz, g.dimz - 1);
+            const int64_t ncl = (int64_t)max(hx - lx + 1, 0) * max(hy - ly + 1, 0) * max(hz - lz + 1, 0);
+            const int64_t nrows = (int64_t)max(hy - ly + 1, 0) * max(hz - lz + 1, 0);
+            fallback = false;
+            if (tau < 0.0f || ncl > 4096 || nrows > 256 || (!g.occ && ncl > 256)) {
                 fallback = true;
             } else {
-                m = cj;
-                thr = tj;
+                float t[NRAD];
+                int c[NRAD];
+#pragma unroll
+                for (int j = 0; j < NRAD; ++j) {
+                    const float r = rho * rad_mul(j);
+                    t[j] = fminf(r * r, tau);
+                    c[j] = 0;
+                }
+                auto count = [&](uint32_t, const float4 p) {
+                    const float d = sqdist_pinned(qx, qy, qz, p.x, p.y, p.z);
+#pragma unroll
+                    for (int j = 0; j < NRAD; ++j) c[j] += d <= t[j] ? 1 : 0;
+                };
+                if (g.occ) for_rows(g, qx, qy, qz, lx, hx, ly, hy, lz, hz, eta, t[NRAD - 1], count);
+                else for_box_points(g, qx, qy, qz, lx, hx, ly, hy, lz, hz, eta, t[NRAD - 1], count);
+                int js = -1;
+#pragma unroll
+                for (int j = NRAD - 1; j >= 0; --j)
+                    if (c[j] >= k) js = j;
+                int cj = 0;
+                float tj = -1.0f;
+#pragma unroll
+                for (int j = 0; j < NRAD; ++j)
+                    if (j == js) { cj = c[j]; tj = t[j]; }
+                if (js < 0 || cj > CAP) {
+                    fallback = true;
+                    // too few within the certified radii: widen; too many: narrow
+                    // (unless the certified radius, not the trial radius, was short)
+                    const bool widen = js < 0;
+                    if (!(widen && t[NRAD - 1] >= tau)) {
+                        todo = true;
+                        rho = widen ? rho * 1.8f : rho * 0.7f;
+                    }
+                } else {
+                    m = cj;
+                    thr = tj;
+                }
             }
         }
     }
@@ -844,9 +862,15 @@ __global__ void __launch_bounds__(256, 2) k_knn(Grid g, const float* __restrict_
     extern __shared__ __align__(16) unsigned char smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nwarps = blockDim.x >> 5;
-    const int64_t t = (int64_t)blockIdx.x * nwarps + warp;
+    // Tiles are issued last-first.  A spinning LiDAR scan stored ring by ring
+    // with rising elevation ends with its farthest, sparsest points, whose
+    // tiles cost the most; starting them first lets the cheap near-range
+    // tiles fill the end of the launch.  (The order never changes a result.)
+    const int64_t tiles = (N + tile - 1) / tile;
+    const int64_t w = (int64_t)blockIdx.x * nwarps + warp;
+    if (w >= tiles) return;
+    const int64_t t = a.last_first ? tiles - 1 - w : w;
     const int64_t n0 = t * tile;
-    if (n0 >= N) return;
     const int cnt = (int)min((int64_t)tile, N - n0);
     process_tile<MODE, COV>(g, q, n0, cnt, a, rho0, idx, d2, cov,
                             smem + (size_t)warp * warp_smem_bytes(MODE), lane);
@@ -952,7 +976,7 @@ cudaError_t pc_launch_knn(const pc_target_s* t, const float* q, int64_t N, int k
     if (e != cudaSuccess) return e;
     const int tile = clamp_tile(t->tune.tile);
     const int warps = clamp_warps(t->tune.warps);
-    TileArgs a{k, eps, t->tune.rho_scale > 0 ? t->tune.rho_scale : 0.9f};
+    TileArgs a{k, eps, t->tune.rho_scale > 0 ? t->tune.rho_scale : 0.9f, t->tune.order == 0 ? 1 : 0};
     const bool with_cov = cov != nullptr;
     const int mode = search_mode(k);
     const size_t smem = (size_t)warps * warp_smem_bytes(mode);
@@ -979,7 +1003,7 @@ cudaError_t pc_launch_knn_batch(const pc_target_s* t, const ScanDesc* scans_dev,
                                 int64_t total_tiles, int tile, int warps, int blocks, int k,
                                 float eps, bool with_cov, float rho0,
                                 unsigned long long* counter, cudaStream_t s) {
-    TileArgs a{k, eps, t->tune.rho_scale > 0 ? t->tune.rho_scale : 0.9f};
+    TileArgs a{k, eps, t->tune.rho_scale > 0 ? t->tune.rho_scale : 0.9f, 0};
     const int mode = search_mode(k);
     const size_t smem = (size_t)warps * warp_smem_bytes(mode);
     Grid g = t->g;

@@ -68,6 +68,7 @@ void default_tune(pc_tune* tu) {
     tu->tile = 32;
     tu->warps = 4;
     tu->rho_scale = 0.9f;
+    tu->order = 0;
 }
 
 pc_status read_and_clear_status(pc_target_s* t, cudaStream_t s) {
@@ -226,7 +227,8 @@ pc_status pc_set_tune(pc_target t, const pc_tune* tune) {
         default_tune(&t->tune);
         return PC_OK;
     }
-    if (tune->tile > 32 || tune->warps > 8 || !(std::isfinite(tune->rho_scale)))
+    if (tune->tile > 32 || tune->warps > 8 || !(std::isfinite(tune->rho_scale)) || tune->order < 0 ||
+        tune->order > 1)
         return PC_ERR_INVALID_ARG;
     t->tune = *tune;
     if (t->tune.tile <= 0) t->tune.tile = 32;

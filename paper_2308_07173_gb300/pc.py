@@ -66,7 +66,8 @@ class pc_build_opts(ctypes.Structure):
 
 
 class pc_tune(ctypes.Structure):
-    _fields_ = [("tile", ctypes.c_int), ("warps", ctypes.c_int), ("rho_scale", ctypes.c_float)]
+    _fields_ = [("tile", ctypes.c_int), ("warps", ctypes.c_int), ("rho_scale", ctypes.c_float),
+                ("order", ctypes.c_int)]
 
 
 class pc_target_info(ctypes.Structure):
@@ -312,8 +313,8 @@ class Target:
             "rho_hint": list(i.rho_hint),
         }
 
-    def set_tune(self, tile: int = 0, warps: int = 0, rho_scale: float = 0.0):
-        pc_set_tune(self.handle, pc_tune(tile, warps, rho_scale))
+    def set_tune(self, tile: int = 0, warps: int = 0, rho_scale: float = 0.0, order: int = 0):
+        pc_set_tune(self.handle, pc_tune(tile, warps, rho_scale, order))
 
     def knn(self, q, k: int, idx=None, d2=None, stream=None):
         torch = _torch()

@@ -122,7 +122,8 @@ def test_empty_query_is_noop(c1, gpu_lib):
     assert t.sync_status() == gpu_lib.PC_OK
 
 
-@pytest.mark.parametrize("tune", [(1, 1, 0.5), (7, 3, 3.0), (32, 8, 1.0), (16, 8, 20.0), (32, 2, 0.2)])
+@pytest.mark.parametrize("tune", [(1, 1, 0.5, 0), (7, 3, 3.0, 1), (32, 8, 1.0, 0), (16, 8, 20.0, 1),
+                                  (32, 2, 0.2, 0), (32, 4, 0.9, 1)])
 def test_launch_shape_never_changes_results(c1, gpu_lib, tune):
     p, t = c1
     q = dev(p[::5])
