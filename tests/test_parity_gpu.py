@@ -344,3 +344,55 @@ def test_c2_batch_equals_single_scans(c2, gpu_lib):
     np.testing.assert_array_equal(host(bufs[0][1])[:500], ri)
     assert t.sync_status() == gpu_lib.PC_OK
     b.close()
+
+
+# ---------------------------------------------------------------- uneven occupancy
+@pytest.fixture(scope="module")
+def pit_world(gpu_lib):
+    tr = W.oval_4000_pit()
+    m = tr.sample_map(400_000, seed=61, noise=0.01)
+    g = W.rng_for(62)
+    q = tr.raycast(*tr.random_pose(g), g)[::16].copy()
+    t = gpu_lib.Target(dev(m))
+    tree = oracle.KDTree(m)
+    yield q, m, t, tree
+    t.close()
+
+
+@pytest.mark.parametrize("k", [10, 20, 32])
+def test_uneven_occupancy_map_parity(pit_world, gpu_lib, k):
+    q, m, t, tree = pit_world
+    idx, d2, cov, st = run_knn_cov(gpu_lib, t, q, k, 1e-3)
+    assert st == gpu_lib.PC_OK
+    ri, rd = tree.knn(q, k)
+    np.testing.assert_array_equal(idx, ri)
+    np.testing.assert_array_equal(d2.view(np.uint32), rd.view(np.uint32))
+    raw = host(t.cov(dev(ri), -1.0))
+    H.check_raw_cov(raw, oracle.cov(m, ri, -1.0))
+    H.check_regularised_cov(cov, oracle.cov(m, ri, 1e-3), oracle.cov(m, ri, -1.0), raw, 1e-3)
+
+
+def test_retries_and_fallbacks_stay_exact(gpu_lib):
+    # a dense clump (too many points inside the smallest trial radius), a
+    # sparse surface, and queries well off the surface (too few inside the
+    # largest): the lane path must narrow, widen or hand over, never err
+    rng = np.random.default_rng(71)
+    plane = np.c_[rng.uniform(0, 30, (20000, 2)), np.zeros(20000)]
+    clump = rng.normal([15, 15, 0], 0.002, (3000, 3))
+    p = np.concatenate([plane, clump]).astype(np.float32)
+    q = np.concatenate([
+        np.c_[rng.uniform(1, 29, (300, 2)), rng.normal(0, 0.01, 300)],     # on the plane
+        rng.normal([15, 15, 0], 0.003, (200, 3)),                          # inside the clump
+        np.c_[rng.uniform(1, 29, (200, 2)), rng.uniform(0.5, 3.0, 200)],   # above the plane
+    ]).astype(np.float32)
+    t = gpu_lib.Target(dev(p))
+    for k in (8, 20, 32):
+        t.stats(reset=True)
+        idx, d2, cov, st = run_knn_cov(gpu_lib, t, q, k, -1.0)
+        assert st == gpu_lib.PC_OK
+        ri, rd = oracle.knn_brute(q, p, k)
+        np.testing.assert_array_equal(idx, ri)
+        np.testing.assert_array_equal(d2.view(np.uint32), rd.view(np.uint32))
+        H.check_raw_cov(cov, oracle.cov(p, ri, -1.0))
+        assert t.stats()["queries"] == len(q)
+    t.close()

@@ -78,3 +78,15 @@ def test_batch_scratch_entry_checks_scratch(small_world, gpu_lib):
     ri, rd = t.knn(pts, k)
     torch.cuda.synchronize()
     assert torch.equal(ri, idx) and torch.equal(rd.view(torch.int32), d2.view(torch.int32))
+
+
+def test_tiny_budget_serves_one_scan_at_a_time(small_world, gpu_lib):
+    t, arr = small_world
+    k, eps = 16, -1.0
+    reqs = serve.requests_from_arrivals(arr[:10])
+    serve.prepare(reqs)
+    srv = serve.Server(t, k, eps, hbm_budget=1, max_step_scans=8, slots=2, keep_results=True)
+    rep = srv.serve(reqs, speed=1e6)
+    assert rep["scans"] == 10 and rep["steps"] == 10  # the budget admits one request per step
+    for r in reqs:
+        assert _same(r.out_host, _alone(t, r.points, k, eps))
