@@ -3,36 +3,32 @@
 // C_i of Eq. 19 need every point's k nearest neighbours and the covariance
 // of that neighbourhood -- the step the paper moves from CPU to GPU).
 //
-// One warp owns a tile of up to 32 queries and runs them one at a time:
+// Exactness rests on one fact, certified_tau: for a box of cells around q,
+// every target point outside the box has a binary32 d2 above a computable
+// tau, so any radius t with t^2 <= tau that holds >= k points holds the k
+// nearest.  Two searches use it:
 //
-//  1. Radius-driven box.  With a search radius rho (the previous query's
-//     k-th distance x rho_scale, or the target's calibrated radius), the
-//     cells from cell(q - rho) to cell(q + rho) on each axis are looked up
-//     in the voxel hash, one cell per lane, and their point ranges are
-//     prefix-summed across the warp.
-//  2. Candidates.  32 candidates at a time, one per lane, are read as
-//     coalesced float4 from the cell-sorted copy; each lane computes the
-//     pinned binary32 d2 and the 64-bit key (d2 bits << 32 | index), which
-//     orders exactly like (d2, index).
-//  3. Filter + top-k.  A candidate survives if d2 <= tau (the square of the
-//     radius the box is CERTIFIED to cover, see certified_tau) and it beats
-//     the current k-th key.  Survivors are staged in shared memory; every 32
-//     of them are bitonic-sorted across the warp with shuffles and merged
-//     into the register-resident top-k (lane l holds rank l, and rank 32+l
-//     for k > 32).
-//  4. Stop or widen.  If k survivors exist, every point outside the box or
-//     beyond tau is provably farther than the k-th, so the answer is exact.
-//     Otherwise rho grows and the box is scanned again; past max_box_cells
-//     an exact scan over all occupied cells (with per-cell lower bounds)
-//     takes over, or the row is marked PC_ERR_SEARCH_LIMIT.
-//  5. Epilogue (fused form).  Once the tile is done, lane i computes query
-//     i's covariance from the neighbour indices staged in shared memory:
-//     a two-pass binary32 mean/centred sum shifted by the nearest
-//     neighbour, then -- for eps >= 0 -- a binary32 Jacobi eigen-solve
-//     for the normal n and C' = I - (1-eps) n n^T.
+// * Lane path (k <= 32; lane_tile) -- one query per lane of a 32-query
+//   tile.  Pass 1 walks the rows of the box (occupancy bitmap + rank, one
+//   contiguous point range per row) and counts points under eight trial
+//   radii; the smallest radius holding >= k (and <= the survivor cap)
+//   wins, a failing lane retries with the radii scaled, and pass 2
+//   collects the winners' positions in shared memory.  A register bitonic
+//   network sorts 32-bit keys (d2 bits with a slot tag), an exact fix-up
+//   orders equal buckets by (d2, index), and the covariance reads the k
+//   neighbours from the cell-sorted copy in rank order.
+// * Warp path (k > 32, and the lane path's leftovers; knn_search) -- one
+//   query per warp: the cells of a radius-driven box are looked up in the
+//   voxel hash one per lane, candidates arrive 32 at a time as coalesced
+//   float4 loads, survivors of the certified filter are merged into a
+//   register top-k by bitonic shuffles, and the radius widens until k are
+//   certified; past max_box_cells an exact scan over all occupied cells
+//   (or PC_ERR_SEARCH_LIMIT) ends it.
 //
-// Everything is exact/deterministic by construction: the tile, the launch
-// shape, rho and the batching never change a result bit.
+// The covariance is a two-pass binary32 mean/centred sum shifted by the
+// nearest neighbour; for eps >= 0 a binary32 Jacobi eigen-solve gives the
+// normal n and C' = I - (1-eps) n n^T.  Nothing here changes a result bit
+// with the tile, launch shape, radii, tile order or batching.
 #include <cmath>
 #include <cstdint>
 #include <mutex>
@@ -1012,8 +1008,6 @@ cudaError_t pc_launch_knn_batch(const pc_target_s* t, const ScanDesc* scans_dev,
         return cudaLaunchKernel(kern, dim3((unsigned)blocks), dim3(warps * 32), args, smem, s);
     });
 }
-
-size_t pc_knn_smem_per_warp(int k, bool) { return warp_smem_bytes(search_mode(k)); }
 
 int pc_knn_batch_blocks(int k, bool with_cov, int warps) {
     int dev = 0, sms = 0, per_sm = 0;

@@ -78,7 +78,6 @@ cudaError_t pc_launch_knn_batch(const pc_target_s* t, const ScanDesc* scans_dev,
                                 int64_t total_tiles, int tile, int warps, int blocks, int k,
                                 float eps, bool with_cov, float rho0,
                                 unsigned long long* counter, cudaStream_t s);
-size_t pc_knn_smem_per_warp(int k, bool with_cov);
 int pc_knn_batch_blocks(int k, bool with_cov, int warps);
 
 // pc_api.cu
