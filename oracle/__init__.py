@@ -14,6 +14,8 @@ Functions follow the plain definitions:
   for eps >= 0 the plane regularisation C' = I - (1-eps) n n^T with n the
   smallest-eigenvalue eigenvector (cyclic Jacobi).
 * ``eig_sym3(c6)``         -- the Jacobi eigen-solver on its own.
+* ``gicp_transform`` / ``gicp_linearize`` -- one Gauss-Newton linearisation
+  of GICP (Eq. 18-20) in binary64 on top of the nearest-point search.
 
 Parity of the covariance against the paper's own numbers is unpinned: the
 paper prints no worked example.  The pins live in ``tests/test_oracle_pins.py``
@@ -62,6 +64,10 @@ def _load():
         lib.oracle_cov.restype = i32
         lib.oracle_eig_sym3.argtypes = [vp, vp, vp]
         lib.oracle_eig_sym3.restype = None
+        lib.oracle_gicp_linearize.argtypes = [vp, vp, vp, i64, vp, vp, ctypes.c_float, vp, vp, i32]
+        lib.oracle_gicp_linearize.restype = i32
+        lib.oracle_gicp_transform.argtypes = [vp, vp, i64, vp]
+        lib.oracle_gicp_transform.restype = None
         lib.oracle_default_threads.argtypes = []
         lib.oracle_default_threads.restype = i32
         _lib = lib
@@ -125,6 +131,42 @@ class KDTree:
             self.close()
         except Exception:
             pass
+
+
+def gicp_transform(pose, src) -> np.ndarray:
+    """p' = R p + t in binary32 with the pinned order
+    fmaf(R_a2, p_z, fmaf(R_a1, p_y, fmaf(R_a0, p_x, t_a))); pose = (R 3x3
+    row-major, t 3)."""
+    pose = np.ascontiguousarray(pose, dtype=np.float32).reshape(12)
+    src = _f32x3(src)
+    out = np.empty_like(src)
+    _load().oracle_gicp_transform(_ptr(pose), _ptr(src), src.shape[0], _ptr(out))
+    return out
+
+
+def gicp_linearize(tree: "KDTree", map_cov, src, src_cov, pose, max_dist: float, threads: int = 0) -> dict:
+    """One Gauss-Newton linearisation of GICP (Eq. 18-20) in binary64: the
+    source points moved by pose (gicp_transform), each paired with its nearest
+    map point of tree when d2 <= fl(max_dist^2), Omega = (C_q + R C_p R^T)^-1,
+    H = sum J^T Omega J, b = sum J^T Omega d, E = sum d^T Omega d with
+    d = q - p' and J = [[p']_x, -I] (left perturbation, xi = (omega, v)).
+    Returns {H [6,6], b [6], error, pairs, corr [n] (map index or -1)}."""
+    map_cov = np.ascontiguousarray(map_cov, dtype=np.float32)
+    src = _f32x3(src)
+    src_cov = np.ascontiguousarray(src_cov, dtype=np.float32)
+    if map_cov.shape != (tree.m, 6) or src_cov.shape != (src.shape[0], 6):
+        raise ValueError("covariances must be [m,6] and [n,6]")
+    pose = np.ascontiguousarray(pose, dtype=np.float32).reshape(12)
+    out = np.empty(29, np.float64)
+    corr = np.empty(src.shape[0], np.int32)
+    rc = _load().oracle_gicp_linearize(tree._h, _ptr(map_cov), _ptr(src), src.shape[0], _ptr(src_cov), _ptr(pose),
+                                       float(max_dist), _ptr(out), _ptr(corr), int(threads))
+    if rc != 0:
+        raise ValueError("oracle_gicp_linearize: bad arguments")
+    H = np.zeros((6, 6))
+    H[np.triu_indices(6)] = out[:21]
+    H = H + np.triu(H, 1).T
+    return {"H": H, "b": out[21:27].copy(), "error": float(out[27]), "pairs": int(out[28]), "corr": corr}
 
 
 def cov(p, idx, eps: float, threads: int = 0) -> np.ndarray:

@@ -472,3 +472,133 @@ int oracle_cov(const float *p, int64_t m, const int32_t *idx, int64_t n, int k, 
     parallel_for(n, nthreads, cov_range, &c);
     return 0;
 }
+
+/* ------------------------------------------------------------------ */
+/* GICP linearisation (Eq. 18-20), one Gauss-Newton step.              */
+/* ------------------------------------------------------------------ */
+/* pose = R (row-major 3x3) then t (3), binary32.  Every source point p is
+ * moved to p' = R p + t in binary32 with the pinned order
+ *     p'_a = fmaf(R_a2, p_z, fmaf(R_a1, p_y, fmaf(R_a0, p_x, t_a)))
+ * and matched to its nearest map point q (d2 and ties as in the kNN above).
+ * The pair is an inlier when p' is finite and d2 <= fl(max_dist^2).
+ *
+ * In binary64, with the residual d = q - p' (Eq. 18) and the combined
+ * covariance S = C_q + R C_p R^T (Eq. 19; the printed form of that sum is
+ * garbled, this is the standard GICP one), Omega = S^-1 and the step sums
+ *     H = sum J^T Omega J,  b = sum J^T Omega d,  E = sum d^T Omega d
+ * over the inliers whose S has a positive determinant, with
+ * J = [ [p']_x , -I ] the derivative of d under the left perturbation
+ * T <- exp(xi^) T, xi = (omega, v): T p ~ p' + omega x p' + v.
+ * Minimising sum (d + J xi)^T Omega (d + J xi) gives H xi = -b.
+ *
+ * out (29 doubles): H upper triangle row by row (21), b (6), E, the number
+ * of pairs summed.  corr (optional, [n]): the map index of each inlier
+ * pair, -1 for the others. */
+void oracle_gicp_transform(const float *pose, const float *src, int64_t n, float *out)
+{
+    for (int64_t i = 0; i < n; i++) {
+        const float *p = src + 3 * i;
+        for (int a = 0; a < 3; a++)
+            out[3 * i + a] =
+                fmaf(pose[3 * a + 2], p[2], fmaf(pose[3 * a + 1], p[1], fmaf(pose[3 * a + 0], p[0], pose[9 + a])));
+    }
+}
+
+static void sym6_to_mat(const float *c, double M[3][3])
+{
+    M[0][0] = c[0]; M[0][1] = c[1]; M[0][2] = c[2];
+    M[1][0] = c[1]; M[1][1] = c[3]; M[1][2] = c[4];
+    M[2][0] = c[2]; M[2][1] = c[4]; M[2][2] = c[5];
+}
+
+/* Inverse of a symmetric 3x3 as adjugate / determinant; returns 0 (and
+ * leaves O alone) when the determinant is not positive. */
+static int inv_sym3(double S[3][3], double O[3][3])
+{
+    const double a00 = S[1][1] * S[2][2] - S[1][2] * S[2][1];
+    const double a01 = S[0][2] * S[2][1] - S[0][1] * S[2][2];
+    const double a02 = S[0][1] * S[1][2] - S[0][2] * S[1][1];
+    const double a11 = S[0][0] * S[2][2] - S[0][2] * S[2][0];
+    const double a12 = S[0][2] * S[1][0] - S[0][0] * S[1][2];
+    const double a22 = S[0][0] * S[1][1] - S[0][1] * S[1][0];
+    const double det = S[0][0] * a00 + S[1][0] * a01 + S[2][0] * a02;
+    if (!(det > 0)) return 0;
+    O[0][0] = a00 / det; O[0][1] = a01 / det; O[0][2] = a02 / det;
+    O[1][0] = a01 / det; O[1][1] = a11 / det; O[1][2] = a12 / det;
+    O[2][0] = a02 / det; O[2][1] = a12 / det; O[2][2] = a22 / det;
+    return 1;
+}
+
+int oracle_gicp_linearize(void *vt, const float *map_cov, const float *src, int64_t n, const float *src_cov,
+                          const float *pose, float max_dist, double *out, int32_t *corr, int nthreads)
+{
+    kdtree *t = (kdtree *)vt;
+    if (!t || n < 0 || !(max_dist >= 0)) return -1;
+    const int64_t nn_ = n > 0 ? n : 1;
+    float *moved = (float *)malloc(sizeof(float) * 3 * nn_);
+    float *fin = (float *)malloc(sizeof(float) * 3 * nn_);
+    int64_t *pos = (int64_t *)malloc(sizeof(int64_t) * nn_);
+    int32_t *nb = (int32_t *)malloc(sizeof(int32_t) * nn_);
+    float *nd = (float *)malloc(sizeof(float) * nn_);
+    oracle_gicp_transform(pose, src, n, moved);
+    /* nearest map point of every finite moved point */
+    int64_t nf = 0;
+    for (int64_t i = 0; i < n; i++) {
+        if (corr) corr[i] = -1;
+        if (isfinite(moved[3 * i]) && isfinite(moved[3 * i + 1]) && isfinite(moved[3 * i + 2])) {
+            memcpy(fin + 3 * nf, moved + 3 * i, 3 * sizeof(float));
+            pos[nf++] = i;
+        }
+    }
+    if (nf > 0) oracle_kdtree_knn(vt, fin, nf, 1, nb, nd, nthreads);
+    const float max_d2 = max_dist * max_dist;
+    double R[3][3];
+    for (int a = 0; a < 3; a++)
+        for (int c = 0; c < 3; c++) R[a][c] = pose[3 * a + c];
+    double H[6][6] = {{0}}, b[6] = {0}, E = 0, pairs = 0;
+    for (int64_t f = 0; f < nf; f++) {
+        if (!(nd[f] <= max_d2)) continue;
+        const int64_t i = pos[f];
+        if (corr) corr[i] = nb[f];
+        const float *q = t->p + 3 * (int64_t)nb[f];
+        const double pp[3] = {fin[3 * f], fin[3 * f + 1], fin[3 * f + 2]};
+        const double d[3] = {(double)q[0] - pp[0], (double)q[1] - pp[1], (double)q[2] - pp[2]};
+        double Cq[3][3], Cp[3][3], S[3][3], O[3][3];
+        sym6_to_mat(map_cov + 6 * (int64_t)nb[f], Cq);
+        sym6_to_mat(src_cov + 6 * i, Cp);
+        /* S = Cq + R Cp R^T */
+        for (int a = 0; a < 3; a++)
+            for (int c = 0; c < 3; c++) {
+                double s = 0;
+                for (int e = 0; e < 3; e++)
+                    for (int g = 0; g < 3; g++) s += R[a][e] * Cp[e][g] * R[c][g];
+                S[a][c] = Cq[a][c] + s;
+            }
+        if (!inv_sym3(S, O)) continue;
+        const double J[3][6] = {{0, -pp[2], pp[1], -1, 0, 0},
+                                {pp[2], 0, -pp[0], 0, -1, 0},
+                                {-pp[1], pp[0], 0, 0, 0, -1}};
+        for (int r = 0; r < 6; r++) {
+            for (int c = r; c < 6; c++)
+                for (int a = 0; a < 3; a++)
+                    for (int e = 0; e < 3; e++) H[r][c] += J[a][r] * O[a][e] * J[e][c];
+            for (int a = 0; a < 3; a++)
+                for (int e = 0; e < 3; e++) b[r] += J[a][r] * O[a][e] * d[e];
+        }
+        for (int a = 0; a < 3; a++)
+            for (int e = 0; e < 3; e++) E += d[a] * O[a][e] * d[e];
+        pairs += 1;
+    }
+    int w = 0;
+    for (int r = 0; r < 6; r++)
+        for (int c = r; c < 6; c++) out[w++] = H[r][c];
+    for (int r = 0; r < 6; r++) out[w++] = b[r];
+    out[w++] = E;
+    out[w++] = pairs;
+    free(moved);
+    free(fin);
+    free(pos);
+    free(nb);
+    free(nd);
+    return 0;
+}
