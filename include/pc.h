@@ -239,6 +239,69 @@ PC_API pc_status pc_batch_run_scratch(pc_target t, const pc_scan *scans, int n_s
 PC_API pc_status pc_batch_run_noalloc(pc_target t, const pc_scan *scans, int n_scans, int k,
                                       float eps, pc_stream s);
 
+/* ---- GICP registration on top of the search (Sec. III-C1, Eq. 18-20) ---- */
+
+/* Number of doubles pc_gicp_linearize writes to out_dev. */
+#define PC_GICP_OUT 29
+
+/* Bytes of device workspace pc_gicp_linearize needs on the current device
+ * (a ticket counter and one partial-sum row per resident block; ~80 KB on
+ * a 152-SM GPU); 0 if no device is usable. */
+PC_API size_t pc_gicp_work_bytes(void);
+
+/* One Gauss-Newton linearisation of scan-to-map GICP (Sec. III-C1: the
+ * transformation error d_i of Eq. 18, its covariance of Eq. 19 and the
+ * objective of Eq. 20), with the map the target `map` was built from.
+ *
+ *  map_cov_dev  f32 [M,6] packed (xx xy xz yy yz zz) covariance C_q of every
+ *               map point, in the caller's map order (e.g. pc_knn_cov of the
+ *               map against itself).
+ *  src_dev      f32 [n,3] source scan points p; src_cov_dev f32 [n,6] their
+ *               covariances C_p (pc_knn_cov of the scan against a target
+ *               built from the scan).
+ *  pose_dev     f32 [12] device-resident pose: R row-major (9) then t (3).
+ *  max_dist     correspondence distance: a source point pairs with its
+ *               exact nearest map point q (pinned binary32 d2, ties to the
+ *               lower index) when d2 <= fl(max_dist^2); +inf pairs all.
+ *  out_dev      f64 [29]: H upper triangle row by row (21), b (6), E, the
+ *               number of pairs summed, where with p' = R p + t (binary32,
+ *               fmaf(R_a2,p_z, fmaf(R_a1,p_y, fmaf(R_a0,p_x, t_a)))),
+ *               d = q - p', Omega = (C_q + R C_p R^T)^-1 and
+ *               J = [[p']_x, -I] (left perturbation T <- exp(xi^) T,
+ *               xi = (omega, v)):  H = sum J^T Omega J,
+ *               b = sum J^T Omega d,  E = sum d^T Omega d.  A pair whose
+ *               combined covariance is not positive definite (binary32
+ *               determinant <= 0) is matched but not summed.  Per pair the
+ *               terms are binary32; the sums are binary64 in a fixed
+ *               order, so the same call repeats bit for bit.
+ *  corr_dev     optional i32 [n]: the map index of each pair, -1 for a
+ *               point with no map point within max_dist or a non-finite p'.
+ *  work_dev     device workspace of at least pc_gicp_work_bytes() bytes,
+ *               256-byte aligned, owned by the caller; calls that share it
+ *               must not overlap on the GPU.
+ * Asynchronous on `s`; allocates nothing.  Errors: PC_ERR_INVALID_ARG for
+ * n < 0, a NaN or negative max_dist, a NULL, misaligned or too small
+ * argument; PC_ERR_BAD_POINTER for host pointers; a destroyed or foreign
+ * handle as for pc_knn.  A non-finite p' sets PC_ERR_NONFINITE, a search
+ * that passed max_box_cells with exhaustive = 0 PC_ERR_SEARCH_LIMIT in the
+ * status word (pc_sync_status); such points do not pair. */
+PC_API pc_status pc_gicp_linearize(pc_target map, const float *map_cov_dev, const float *src_dev,
+                                   int64_t n, const float *src_cov_dev, const float *pose_dev,
+                                   float max_dist, double *out_dev, int32_t *corr_dev,
+                                   void *work_dev, size_t work_bytes, pc_stream s);
+
+/* The Gauss-Newton (lambda = 0) or Levenberg-Marquardt (lambda > 0) step
+ * after pc_gicp_linearize, on the device: solves (H + lambda I) xi = -b by
+ * Cholesky in binary64 from lin_dev (the 29 doubles above) and moves the
+ * pose in place, R <- Exp(omega) R, t <- Exp(omega) t + v (Rodrigues).
+ * xi_dev (optional, f64 [6]) receives xi, or NaNs when H + lambda I is not
+ * positive definite (the pose is then left unchanged).  One single-thread
+ * launch on `s`, so linearise + update iterations queue (or graph-capture)
+ * with no host round trip.  PC_ERR_INVALID_ARG for NULL lin/pose or a
+ * negative or NaN lambda, PC_ERR_BAD_POINTER for host pointers. */
+PC_API pc_status pc_gicp_update(const double *lin_dev, float lambda, float *pose_dev,
+                                double *xi_dev, pc_stream s);
+
 PC_API const char *pc_status_string(pc_status st);
 
 /* Library version string, e.g. "pc 0.1 sm_103a". */

@@ -16,6 +16,8 @@ Functions follow the plain definitions:
 * ``eig_sym3(c6)``         -- the Jacobi eigen-solver on its own.
 * ``gicp_transform`` / ``gicp_linearize`` -- one Gauss-Newton linearisation
   of GICP (Eq. 18-20) in binary64 on top of the nearest-point search.
+* ``gicp_update`` / ``so3_exp`` -- the step that follows it: solve
+  (H + lam I) xi = -b, move the pose by Exp(omega) on the left.
 
 Parity of the covariance against the paper's own numbers is unpinned: the
 paper prints no worked example.  The pins live in ``tests/test_oracle_pins.py``
@@ -167,6 +169,31 @@ def gicp_linearize(tree: "KDTree", map_cov, src, src_cov, pose, max_dist: float,
     H[np.triu_indices(6)] = out[:21]
     H = H + np.triu(H, 1).T
     return {"H": H, "b": out[21:27].copy(), "error": float(out[27]), "pairs": int(out[28]), "corr": corr}
+
+
+def so3_exp(w) -> np.ndarray:
+    """Rotation matrix of the rotation vector w by the Rodrigues formula
+    I + sin(th)/th [w]_x + (1 - cos(th))/th^2 [w]_x^2 (binary64)."""
+    w = np.asarray(w, np.float64).reshape(3)
+    th = float(np.sqrt(w @ w))
+    K = np.array([[0, -w[2], w[1]], [w[2], 0, -w[0]], [-w[1], w[0], 0]], np.float64)
+    if th == 0.0:
+        return np.eye(3)
+    return np.eye(3) + np.sin(th) / th * K + (1.0 - np.cos(th)) / (th * th) * (K @ K)
+
+
+def gicp_update(pose, H, b, lam: float = 0.0):
+    """The Gauss-Newton (lam = 0) or Levenberg-Marquardt step after a
+    linearisation: xi = (H + lam I)^-1 (-b), then R <- Exp(omega) R,
+    t <- Exp(omega) t + v (xi = (omega, v)).  Returns (pose float32 [12],
+    xi float64 [6]); pose rounded once from binary64."""
+    pose = np.asarray(pose, np.float32).reshape(12).astype(np.float64)
+    A = np.asarray(H, np.float64) + float(lam) * np.eye(6)
+    xi = np.linalg.solve(A, -np.asarray(b, np.float64))
+    E = so3_exp(xi[:3])
+    R = pose[:9].reshape(3, 3)
+    t = pose[9:]
+    return np.concatenate([(E @ R).ravel(), E @ t + xi[3:]]).astype(np.float32), xi
 
 
 def cov(p, idx, eps: float, threads: int = 0) -> np.ndarray:

@@ -528,6 +528,51 @@ void pc_batch_destroy(pc_batch b) {
     delete b;
 }
 
+size_t pc_gicp_work_bytes(void) { return pc_gicp_work_size(); }
+
+pc_status pc_gicp_linearize(pc_target map, const float* map_cov_dev, const float* src_dev,
+                            int64_t n, const float* src_cov_dev, const float* pose_dev,
+                            float max_dist, double* out_dev, int32_t* corr_dev, void* work_dev,
+                            size_t work_bytes, pc_stream s) {
+    pc_status r = check_target(map);
+    if (r != PC_OK) return r;
+    if (n < 0 || n > ((int64_t)1 << 40) || !(max_dist >= 0.0f)) return PC_ERR_INVALID_ARG;
+    if (!out_dev || (reinterpret_cast<uintptr_t>(out_dev) & 7u)) return PC_ERR_INVALID_ARG;
+    if (!is_device_ptr(out_dev)) return PC_ERR_BAD_POINTER;
+    if (n == 0) {  // nothing to pair: all sums zero (the inputs may be empty tensors)
+        DeviceGuard dg(map->device);
+        return pc_from_cuda(cudaMemsetAsync(out_dev, 0, PC_GICP_OUT * sizeof(double), (cudaStream_t)s));
+    }
+    if (!map_cov_dev || !src_dev || !src_cov_dev || !pose_dev || !work_dev) return PC_ERR_INVALID_ARG;
+    if ((reinterpret_cast<uintptr_t>(out_dev) & 7u) || (reinterpret_cast<uintptr_t>(work_dev) & 255u))
+        return PC_ERR_INVALID_ARG;
+    if (!is_device_ptr(map_cov_dev) || !is_device_ptr(src_dev) || !is_device_ptr(src_cov_dev) ||
+        !is_device_ptr(pose_dev) || !is_device_ptr(out_dev) || !is_device_ptr(work_dev) ||
+        (corr_dev && !is_device_ptr(corr_dev)))
+        return PC_ERR_BAD_POINTER;
+    DeviceGuard dg(map->device);
+    const size_t need = pc_gicp_work_size();
+    if (need == 0) return PC_ERR_CUDA;
+    if (work_bytes < need) return PC_ERR_INVALID_ARG;
+    // start radius: the calibrated distance to the nearest other map point
+    float r0 = pc_rho0(map, map->g.m >= 2 ? 2 : 1);
+    if (!(r0 > 0.0f)) r0 = map->g.h;
+    return pc_from_cuda(pc_launch_gicp_linearize(map, map_cov_dev, src_dev, n, src_cov_dev, pose_dev,
+                                                 max_dist, out_dev, corr_dev, work_dev, r0,
+                                                 (cudaStream_t)s));
+}
+
+pc_status pc_gicp_update(const double* lin_dev, float lambda, float* pose_dev, double* xi_dev,
+                         pc_stream s) {
+    if (!lin_dev || !pose_dev || !(lambda >= 0.0f)) return PC_ERR_INVALID_ARG;
+    if ((reinterpret_cast<uintptr_t>(lin_dev) & 7u) || (reinterpret_cast<uintptr_t>(xi_dev) & 7u) ||
+        (reinterpret_cast<uintptr_t>(pose_dev) & 3u))
+        return PC_ERR_INVALID_ARG;
+    if (!is_device_ptr(lin_dev) || !is_device_ptr(pose_dev) || (xi_dev && !is_device_ptr(xi_dev)))
+        return PC_ERR_BAD_POINTER;
+    return pc_from_cuda(pc_launch_gicp_update(lin_dev, lambda, pose_dev, xi_dev, (cudaStream_t)s));
+}
+
 const char* pc_status_string(pc_status st) {
     switch (st) {
         case PC_OK: return "ok";

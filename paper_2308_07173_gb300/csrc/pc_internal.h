@@ -80,6 +80,15 @@ cudaError_t pc_launch_knn_batch(const pc_target_s* t, const ScanDesc* scans_dev,
                                 unsigned long long* counter, cudaStream_t s);
 int pc_knn_batch_blocks(int k, bool with_cov, int warps);
 
+// gicp.cu
+size_t pc_gicp_work_size();
+cudaError_t pc_launch_gicp_linearize(const pc_target_s* t, const float* map_cov, const float* src,
+                                     int64_t n, const float* src_cov, const float* pose,
+                                     float max_dist, double* out, int32_t* corr, void* work,
+                                     float r0, cudaStream_t s);
+cudaError_t pc_launch_gicp_update(const double* lin, float lambda, float* pose, double* xi,
+                                  cudaStream_t s);
+
 // pc_api.cu
 float pc_rho0(const pc_target_s* t, int k);
 pc_status pc_from_cuda(cudaError_t e);

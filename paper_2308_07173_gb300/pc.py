@@ -29,6 +29,7 @@ PC_ERR_BAD_POINTER = 7
 PC_ERR_BAD_INDEX = 8
 PC_ERR_DESTROYED = 9
 PC_NOALLOC_MAX_SCANS = 256
+PC_GICP_OUT = 29
 
 _STATUS_NAMES = {
     0: "PC_OK",
@@ -119,6 +120,9 @@ SIGNATURES = {
     "pc_batch_run_noalloc": (_INT, [_VP, ctypes.POINTER(pc_scan), _INT, _INT, _F, _VP]),
     "pc_batch_scratch_bytes": (ctypes.c_size_t, [_INT]),
     "pc_batch_run_scratch": (_INT, [_VP, ctypes.POINTER(pc_scan), _INT, _INT, _F, _VP, ctypes.c_size_t, _VP]),
+    "pc_gicp_work_bytes": (ctypes.c_size_t, []),
+    "pc_gicp_linearize": (_INT, [_VP, _VP, _VP, _I64, _VP, _VP, _F, _VP, _VP, _VP, ctypes.c_size_t, _VP]),
+    "pc_gicp_update": (_INT, [_VP, _F, _VP, _VP, _VP]),
     "pc_status_string": (ctypes.c_char_p, [_INT]),
     "pc_version": (ctypes.c_char_p, []),
 }
@@ -230,6 +234,20 @@ def pc_batch_run_scratch(t, scans: Sequence[pc_scan], k: int, eps: float, scratc
                          scratch_bytes: int, stream) -> int:
     arr = (pc_scan * len(scans))(*scans)
     return load().pc_batch_run_scratch(t, arr, len(scans), k, eps, scratch_dev, scratch_bytes, stream)
+
+
+def pc_gicp_work_bytes() -> int:
+    return int(load().pc_gicp_work_bytes())
+
+
+def pc_gicp_linearize(t, map_cov_dev, src_dev, n, src_cov_dev, pose_dev, max_dist, out_dev, corr_dev,
+                      work_dev, work_bytes, stream) -> int:
+    return load().pc_gicp_linearize(t, map_cov_dev, src_dev, n, src_cov_dev, pose_dev, max_dist, out_dev,
+                                    corr_dev, work_dev, work_bytes, stream)
+
+
+def pc_gicp_update(lin_dev, lam, pose_dev, xi_dev, stream) -> int:
+    return load().pc_gicp_update(lin_dev, lam, pose_dev, xi_dev, stream)
 
 
 def pc_batch_destroy(b) -> None:
@@ -367,6 +385,40 @@ class Target:
         rc = pc_knn_cov_host(self.handle, qp, n, k, float(eps), ptrs[0], ptrs[1], ptrs[2], _stream_handle(stream))
         _check(rc, "pc_knn_cov_host")
         return out
+
+    def gicp_work(self):
+        """A device workspace for gicp_linearize (kept on the handle; calls
+        that share it must not overlap on the GPU)."""
+        torch = _torch()
+        if getattr(self, "_gicp_work", None) is None:
+            nb = pc_gicp_work_bytes()
+            if nb <= 0:
+                raise PcError(PC_ERR_CUDA, "pc_gicp_work_bytes")
+            self._gicp_work = torch.zeros(nb, dtype=torch.uint8, device=self.device)
+        return self._gicp_work
+
+    def gicp_linearize(self, map_cov, src, src_cov, pose, max_dist: float, out=None, corr=None, work=None,
+                       stream=None):
+        """One GICP linearisation against this target (the map): returns the
+        f64 [29] device tensor (H upper triangle, b, E, pairs) and corr."""
+        torch = _torch()
+        map_cov = _dev_tensor(map_cov, torch.float32, 6, "map_cov")
+        src = _dev_tensor(src, torch.float32, 3, "src")
+        src_cov = _dev_tensor(src_cov, torch.float32, 6, "src_cov")
+        pose = _dev_tensor(pose, torch.float32, None, "pose")
+        if pose.numel() != 12:
+            raise ValueError("pose must hold 12 floats (R row-major, t)")
+        n = src.shape[0]
+        if map_cov.shape[0] != self.m or src_cov.shape[0] != n:
+            raise ValueError("map_cov must be [M,6] for this target and src_cov [n,6] for src")
+        out = out if out is not None else torch.empty(PC_GICP_OUT, dtype=torch.float64, device=src.device)
+        work = work if work is not None else self.gicp_work()
+        cp = corr.data_ptr() if corr is not None else None
+        rc = pc_gicp_linearize(self.handle, map_cov.data_ptr(), src.data_ptr(), n, src_cov.data_ptr(),
+                               pose.data_ptr(), float(max_dist), out.data_ptr(), cp, work.data_ptr(),
+                               work.numel(), _stream_handle(stream))
+        _check(rc, "pc_gicp_linearize")
+        return out, corr
 
     def stats(self, reset: bool = False, stream=None) -> dict:
         st = pc_get_stats(self.handle, _stream_handle(stream), reset)

@@ -63,3 +63,35 @@ def check_regularised_cov(gpu6, ref6, raw_ref6, raw_gpu6, eps, rtol=COV_RTOL):
     bad = np.nonzero(~ok)[0]
     assert bad.size == 0, f"{bad.size} rows over tolerance, e.g. {bad[:5]} err {err[bad[:5]]} gap/tr {(gap / tr)[bad[:5]]}"
     return float(plain.mean())
+
+
+U32 = 2.0 ** -24
+
+
+def gicp_tolerance(eps_reg: float) -> float:
+    """Relative bound for the GPU's GICP sums against the binary64 oracle.
+
+    Per pair the GPU works in binary32.  For plane-regularised covariances
+    (eigenvalues {1, 1, eps}) the combined S = C_q + R C_p R^T has
+    eigenvalues in [2 eps, 2] with the middle one >= 1, and the adjugate
+    inverse with the rounding of S gives an Omega whose error, measured in
+    Omega's own metric (|x^T dOmega y| <= g sqrt(x^T Omega x  y^T Omega y)),
+    is below about 20 u / eps; the residual, the Jacobian products and the
+    32-lane binary32 sum add a few u more.  Summed over pairs,
+    Cauchy-Schwarz turns this into |dH_rc| <= tau sqrt(H_rr H_cc),
+    |db_r| <= tau sqrt(H_rr E) and |dE| <= tau E with tau below."""
+    return 32.0 * U32 / eps_reg + 16.0 * U32
+
+
+def check_gicp(got: dict, want: dict, tau: float) -> dict:
+    """Asserts the bound of gicp_tolerance; returns the worst ratios."""
+    assert got["pairs"] == want["pairs"]
+    Hd = np.diag(want["H"]).copy()
+    scaleH = np.sqrt(np.outer(Hd, Hd))
+    scaleb = np.sqrt(Hd * want["error"])
+    rh = np.abs(got["H"] - want["H"]) / np.maximum(scaleH, 1e-300)
+    rb = np.abs(got["b"] - want["b"]) / np.maximum(scaleb, 1e-300)
+    re = abs(got["error"] - want["error"]) / max(want["error"], 1e-300)
+    worst = {"H": float(rh.max()), "b": float(rb.max()), "E": float(re)}
+    assert worst["H"] <= tau and worst["b"] <= tau and worst["E"] <= tau, (worst, tau)
+    return worst

@@ -250,3 +250,24 @@ def test_bad_max_dist_is_rejected():
     for bad in (-1.0, np.nan):
         with pytest.raises(ValueError):
             oracle.gicp_linearize(oracle.KDTree(q), ISO[None], q, ISO[None], _pose(np.eye(3), [0, 0, 0]), bad)
+
+
+def test_so3_exp_matches_scipy_rotation():
+    rng = np.random.default_rng(7)
+    for w in [np.zeros(3), np.array([1e-9, 0, 0]), *rng.standard_normal((6, 3)), np.array([np.pi - 1e-3, 0, 0])]:
+        np.testing.assert_allclose(oracle.so3_exp(w), Rotation.from_rotvec(w).as_matrix(), atol=1e-14)
+
+
+def test_gicp_update_step_solves_the_normal_equations():
+    rng = np.random.default_rng(8)
+    A = rng.standard_normal((6, 6))
+    H = A @ A.T + 0.1 * np.eye(6)
+    b = rng.standard_normal(6)
+    R = Rotation.from_rotvec([0.1, -0.2, 0.3]).as_matrix()
+    pose = _pose(R, [1.0, 2.0, 3.0])
+    for lam in (0.0, 0.5):
+        new, xi = oracle.gicp_update(pose, H, b, lam)
+        np.testing.assert_allclose((H + lam * np.eye(6)) @ xi, -b, atol=1e-12)
+        Rw = Rotation.from_rotvec(xi[:3]).as_matrix()
+        np.testing.assert_allclose(new[:9].reshape(3, 3), Rw @ pose[:9].reshape(3, 3).astype(np.float64), atol=1e-6)
+        np.testing.assert_allclose(new[9:], Rw @ pose[9:].astype(np.float64) + xi[3:], atol=1e-6)
