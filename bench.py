@@ -41,7 +41,8 @@ EPS = 1e-3
 MAP_POINTS = 2_000_000
 FLUSH_BYTES = 256 << 20  # > 129 MB L2
 FALLBACK_HBM_GBS = 6800.0
-KERNEL_SOURCES = ["paper_2308_07173_gb300/csrc/knn_cov.cu", "paper_2308_07173_gb300/csrc/pc_device.cuh"]
+KERNEL_SOURCES = ["paper_2308_07173_gb300/csrc/knn_cov.cu", "paper_2308_07173_gb300/csrc/pc_device.cuh",
+                  "paper_2308_07173_gb300/csrc/pc_search.cuh"]
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "knn_cov_c2_ncu.json")
 
 
@@ -215,7 +216,7 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--ref-sample", type=int, default=16384)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4", "c5"],
+    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4", "c5", "gicp"],
                     help="c2 is the headline; the others print their own line")
     ap.add_argument("--duration", type=float, default=3.0, help="c4: seconds of arrivals")
     args = ap.parse_args()
@@ -224,7 +225,7 @@ def main():
     if args.impl == "reference":
         return run_reference(args)
     if args.workload != "c2":
-        return {"c1": run_c1, "c3": run_c3, "c4": run_c4, "c5": run_c5}[args.workload](args)
+        return {"c1": run_c1, "c3": run_c3, "c4": run_c4, "c5": run_c5, "gicp": run_gicp}[args.workload](args)
     return run_c2(args)
 
 
@@ -530,6 +531,75 @@ def run_c5(args):
                     "algorithmic_bytes_queries_only": alg},
           search_paths={"warp_search_frac": st["warp_search"] / max(1, st["queries"]),
                         "exhaustive": st["exhaustive"]})
+    return 0
+
+
+def run_gicp(args):
+    """GICP on the C2 scan (131k points) against the 2M-point map: one
+    linearisation (exact nearest-point pairing within 1 m, the combined
+    covariance and the 6x6 normal equations) per step, then a 10-iteration
+    registration (linearise + device-side update) replayed as a CUDA graph."""
+    import numpy as np
+    import torch
+
+    from paper_2308_07173_gb300 import gicp, pc
+    from paper_2308_07173_gb300 import workloads as W
+
+    pc.load()
+    q, m = W.scan_vs_map(MAP_POINTS)
+    N = len(q)
+    md, qd = torch.from_numpy(m).cuda(), torch.from_numpy(q).cuda()
+    s = torch.cuda.Stream()
+    reg = gicp.Registration(md, k=K_NN, eps=EPS)
+    scov = reg.source_covariances(qd)
+    pose0 = np.concatenate([np.eye(3).ravel(), [0.05, -0.03, 0.01]]).astype(np.float32)
+    pose = torch.from_numpy(pose0).cuda()
+    out = torch.empty(29, dtype=torch.float64, device="cuda")
+    corr = torch.empty(N, dtype=torch.int32, device="cuda")
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    t = reg.map
+    t.gicp_linearize(reg.map_cov, qd, scov, pose, 1.0, out=out, corr=corr, stream=s)
+    s.synchronize()
+    assert t.sync_status(s) == pc.PC_OK
+    pairs = int(out[28].item())
+    used = corr[corr >= 0].long()
+    U_p = int(torch.unique(used).numel())
+    info = t.info()
+    pts = md[torch.unique(used)]
+    o = torch.tensor(info["origin"], device="cuda")
+    cells = torch.floor((pts - o) * (1.0 / info["cell_size"])).long()
+    U_c = int(torch.unique((cells[:, 0] << 42) | (cells[:, 1] << 21) | cells[:, 2]).numel())
+    reps = max(5, min(args.steps, 200))
+    clocks = Clocks(torch.cuda.current_device())
+    clocks.start()
+    ms, all_ms = _timed(lambda: t.gicp_linearize(reg.map_cov, qd, scov, pose, 1.0, out=out, stream=s),
+                        flush, reps, s)
+    iters = 10
+    p2 = torch.from_numpy(pose0).cuda()
+
+    def align():
+        p2.copy_(pose, non_blocking=True)
+        reg.align(qd, scov, p2, iters=iters, max_dist=1.0, graph=True, stream=s)
+
+    ms_reg, _ = _timed(align, flush, max(5, min(args.steps, 50)), s)
+    clk = clocks.stop()
+    assert t.sync_status(s) == pc.PC_OK
+    # algorithmic bytes of one linearisation: the scan and its covariances,
+    # the paired map covariances, the distinct map points and cells touched
+    alg = N * (12 + 24) + pairs * 24 + 16 * U_p + 8 * U_c
+    peak, kind = peaks()
+    ach = alg / (ms / 1e3) / 1e9
+    _line("source points/sec through one GICP linearisation (C2 scan vs 2M-point map)", N / (ms / 1e3), UNIT, ms,
+          args, {"workload": "gicp_c2_scan131k_vs_map2M_maxdist1m", "n_points": N, "pairs": pairs,
+                 "map_points": MAP_POINTS, "l2": "flushed by a 256 MB write before every timed call"},
+          roofline={"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                    "traffic": None, "peak_source": kind, "algorithmic_bytes": alg, "U_p": U_p, "U_c": U_c,
+                    "kernel": "k_gicp_linearize"},
+          registration={"iterations": iters, "ms": ms_reg, "ms_per_iteration": ms_reg / iters,
+                        "registrations_per_s": 1e3 / ms_reg, "graph": True},
+          latency_ms={"p50": all_ms[len(all_ms) // 2], "max": all_ms[-1]}, clocks=clk,
+          gpu_launches=reps)
+    reg.close()
     return 0
 
 
