@@ -41,7 +41,7 @@ EPS = 1e-3
 MAP_POINTS = 2_000_000
 FLUSH_BYTES = 256 << 20  # > 129 MB L2
 FALLBACK_HBM_GBS = 6800.0
-KERNEL_SOURCES = ["paper_2308_07173_gb300/csrc/knn_cov.cu", "paper_2308_07173_gb300/csrc/pc_device.cuh",
+KERNEL_SOURCES = ["paper_2308_07173_gb300/csrc/knn_kernels.cuh", "paper_2308_07173_gb300/csrc/pc_device.cuh",
                   "paper_2308_07173_gb300/csrc/pc_search.cuh"]
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "knn_cov_c2_ncu.json")
 
@@ -216,7 +216,7 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--ref-sample", type=int, default=16384)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4", "c5", "gicp"],
+    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4", "c5", "gicp", "window"],
                     help="c2 is the headline; the others print their own line")
     ap.add_argument("--duration", type=float, default=3.0, help="c4: seconds of arrivals")
     args = ap.parse_args()
@@ -225,7 +225,8 @@ def main():
     if args.impl == "reference":
         return run_reference(args)
     if args.workload != "c2":
-        return {"c1": run_c1, "c3": run_c3, "c4": run_c4, "c5": run_c5, "gicp": run_gicp}[args.workload](args)
+        return {"c1": run_c1, "c3": run_c3, "c4": run_c4, "c5": run_c5, "gicp": run_gicp,
+                "window": run_window}[args.workload](args)
     return run_c2(args)
 
 
@@ -531,6 +532,64 @@ def run_c5(args):
                     "algorithmic_bytes_queries_only": alg},
           search_paths={"warp_search_frac": st["warp_search"] / max(1, st["queries"]),
                         "exhaustive": st["exhaustive"]})
+    return 0
+
+
+def run_window(args):
+    """The C2 scan against a sliding-window submap of the 2M-point map: the
+    window of the race-line station nearest the scan (260 m x 260 m, all
+    heights: the sensor's 120 m range plus margin), set on the resident grid
+    with no rebuild; timed next to the same search over the whole map."""
+    import numpy as np
+    import torch
+
+    from paper_2308_07173_gb300 import pc, windows
+    from paper_2308_07173_gb300 import workloads as W
+
+    pc.load()
+    q, m = W.scan_vs_map(MAP_POINTS)
+    N = len(q)
+    md, qd = torch.from_numpy(m).cuda(), torch.from_numpy(q).cuda()
+    t = pc.Target(md)
+    idx = torch.empty((N, K_NN), dtype=torch.int32, device="cuda")
+    d2 = torch.empty((N, K_NN), dtype=torch.float32, device="cuda")
+    cov = torch.empty((N, 6), dtype=torch.float32, device="cuda")
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    s = torch.cuda.Stream()
+    rw = windows.RaceLineWindows.along(W.oval_1500(), spacing=10.0, half=(130.0, 130.0, float("inf")))
+    reps = max(5, min(args.steps, 200))
+    ms_full, _ = _timed(lambda: t.knn_cov(qd, K_NN, EPS, idx, d2, cov, stream=s), flush, reps, s)
+    station = rw.apply(t, np.median(q, axis=0))
+    lo, hi = rw.window(station)
+    lo_t, hi_t = torch.tensor(lo, device="cuda"), torch.tensor(hi, device="cuda")
+    in_win = int(((md >= lo_t) & (md <= hi_t)).all(1).sum())
+    q_out = int((~((qd >= lo_t) & (qd <= hi_t)).all(1)).sum())
+    clocks = Clocks(torch.cuda.current_device())
+    clocks.start()
+    ms, all_ms = _timed(lambda: t.knn_cov(qd, K_NN, EPS, idx, d2, cov, stream=s), flush, reps, s)
+    clk = clocks.stop()
+    st = t.sync_status(s)
+    assert st == pc.PC_OK, pc.pc_status_string(st)
+    ui = torch.unique(idx.view(-1).long())
+    U_p = int(ui.numel())
+    info = t.info()
+    o = torch.tensor(info["origin"], device="cuda")
+    cells = torch.floor((md[ui] - o) * (1.0 / info["cell_size"])).long()
+    U_c = int(torch.unique((cells[:, 0] << 42) | (cells[:, 1] << 21) | cells[:, 2]).numel())
+    alg = N * (12 + 8 * K_NN + 24) + 12 * U_p + 8 * U_c
+    peak, kind = peaks()
+    ach = alg / (ms / 1e3) / 1e9
+    _line("query points/sec for kNN(k=20)+cov against a 260 m sliding-window submap of the 2M map", N / (ms / 1e3),
+          UNIT, ms, args, {"workload": "window_c2_scan131k_map2M_win260m_k20", "n_queries": N,
+                           "map_points": MAP_POINTS, "window_points": in_win, "queries_outside_window": q_out,
+                           "station": station,
+                           "l2": "flushed by a 256 MB write before every timed call"},
+          roofline={"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                    "traffic": None, "peak_source": kind, "algorithmic_bytes": alg, "U_p": U_p, "U_c": U_c,
+                    "kernel": "k_knn<0,true,true> (window variant)"},
+          whole_map_ms=ms_full, latency_ms={"p50": all_ms[len(all_ms) // 2], "max": all_ms[-1]}, clocks=clk,
+          gpu_launches=reps)
+    t.close()
     return 0
 
 

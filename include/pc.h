@@ -159,6 +159,31 @@ PC_API pc_status pc_knn(pc_target t, const float *q_dev, int64_t N, int k, int32
 PC_API pc_status pc_cov(pc_target t, const int32_t *idx_dev, int64_t N, int k, float eps,
                  float *cov_dev, pc_stream s);
 
+/* An axis-aligned box of the map's coordinates; +-inf bounds are allowed. */
+typedef struct {
+    float lo[3];
+    float hi[3];
+} pc_window;
+
+/* Sliding-window submap (Sec. III-C3: scan matching uses the points of a
+ * window M_i of the unified map M^W, selected per pose through the GPU hash
+ * structure): restricts every later search on this target -- pc_knn,
+ * pc_knn_cov, pc_knn_cov_host, the batched forms and pc_gicp_linearize -- to
+ * the map points p with lo <= p <= hi componentwise, without rebuilding the
+ * grid.  NULL restores the whole map.  Results are exactly those of the same
+ * search over the submap, with indices into the whole map (ties still go to
+ * the lower index).  Search boxes are clipped to the window's cells and
+ * only the window's boundary cells test their points, so the cost follows
+ * the window, not the map.  A query whose window holds fewer than k points
+ * gets idx -1 / d2 +inf / cov NaN and PC_ERR_K_GT_M in the status word (with
+ * exhaustive = 0 it may report PC_ERR_SEARCH_LIMIT instead).  pc_cov is not
+ * affected (it takes the neighbours as given).  The window is copied into
+ * each launch when it is issued; a batch plan keeps the window that was set
+ * when pc_batch_plan was called.  Host-only: no device work, no
+ * synchronisation.  Errors: PC_ERR_INVALID_ARG for a NaN bound or lo > hi
+ * on an axis; the handle errors of pc_knn. */
+PC_API pc_status pc_set_window(pc_target t, const pc_window *w);
+
 /* pc_knn and pc_cov fused in one launch; identical results to the two calls. */
 PC_API pc_status pc_knn_cov(pc_target t, const float *q_dev, int64_t N, int k, float eps,
                      int32_t *idx_dev, float *d2_dev, float *cov_dev, pc_stream s);
@@ -176,8 +201,9 @@ PC_API pc_status pc_knn_cov_host(pc_target t, const float *q_host, int64_t N, in
 PC_API pc_status pc_get_stats(pc_target t, pc_stream s, pc_stats *out, int reset);
 
 /* Synchronises `s`, returns and clears the target's status word: PC_OK, or
- * the first of PC_ERR_NONFINITE, PC_ERR_SEARCH_LIMIT, PC_ERR_BAD_INDEX raised
- * since the last call, or PC_ERR_CUDA if the stream reported an error. */
+ * the first of PC_ERR_NONFINITE, PC_ERR_SEARCH_LIMIT, PC_ERR_BAD_INDEX,
+ * PC_ERR_K_GT_M (a search window held fewer than k points) raised since the
+ * last call, or PC_ERR_CUDA if the stream reported an error. */
 PC_API pc_status pc_sync_status(pc_target t, pc_stream s);
 
 /* Batched form: many scans against one target in ONE persistent launch that

@@ -16,6 +16,8 @@ Functions follow the plain definitions:
 * ``eig_sym3(c6)``         -- the Jacobi eigen-solver on its own.
 * ``gicp_transform`` / ``gicp_linearize`` -- one Gauss-Newton linearisation
   of GICP (Eq. 18-20) in binary64 on top of the nearest-point search.
+* ``window_mask`` / ``knn_window`` -- the search restricted to a box of the
+  map (sliding-window submap, Sec. III-C3).
 * ``gicp_update`` / ``so3_exp`` -- the step that follows it: solve
   (H + lam I) xi = -b, move the pose by Exp(omega) on the left.
 
@@ -169,6 +171,35 @@ def gicp_linearize(tree: "KDTree", map_cov, src, src_cov, pose, max_dist: float,
     H[np.triu_indices(6)] = out[:21]
     H = H + np.triu(H, 1).T
     return {"H": H, "b": out[21:27].copy(), "error": float(out[27]), "pairs": int(out[28]), "corr": corr}
+
+
+def window_mask(p, lo, hi) -> np.ndarray:
+    """Map points inside the box [lo, hi] (componentwise, binary32
+    comparisons): the sliding-window submap of Sec. III-C3."""
+    p = _f32x3(p)
+    lo = np.asarray(lo, np.float32).reshape(3)
+    hi = np.asarray(hi, np.float32).reshape(3)
+    return np.all((p >= lo) & (p <= hi), axis=1)
+
+
+def knn_window(q, p, k: int, lo, hi, threads: int = 0):
+    """kNN over the submap {p in [lo, hi]} with indices into the whole map:
+    the plain definition applied to the submap (its points keep their
+    relative order, so ties still go to the lower whole-map index).  Rows
+    get -1 / +inf when the submap holds fewer than k points."""
+    q, p = _f32x3(q), _f32x3(p)
+    sel = np.nonzero(window_mask(p, lo, hi))[0]
+    n = q.shape[0]
+    if len(sel) < k:
+        return np.full((n, k), -1, np.int32), np.full((n, k), np.inf, np.float32)
+    sub = p[sel]
+    if len(sel) * max(n, 1) <= 50_000_000:
+        i, d = knn_brute(q, sub, k, threads)
+    else:
+        t = KDTree(sub)
+        i, d = t.knn(q, k, threads)
+        t.close()
+    return sel[i].astype(np.int32), d
 
 
 def so3_exp(w) -> np.ndarray:

@@ -66,9 +66,9 @@ __device__ int nearest_within(const Grid& g, float px, float py, float pz, float
         const int ulz = cell_of(__fsub_rn(pz, r), g.oz, g.inv_h);
         const int uhz = cell_of(__fadd_rn(pz, r), g.oz, g.inv_h);
         const float tau = certified_tau(g, px, py, pz, ulx, uhx, uly, uhy, ulz, uhz);
-        const int lx = max(ulx, 0), hx = min(uhx, g.dimx - 1);
-        const int ly = max(uly, 0), hy = min(uhy, g.dimy - 1);
-        const int lz = max(ulz, 0), hz = min(uhz, g.dimz - 1);
+        const int lx = max(ulx, g.wlx), hx = min(uhx, g.whx);
+        const int ly = max(uly, g.wly), hy = min(uhy, g.why);
+        const int lz = max(ulz, g.wlz), hz = min(uhz, g.whz);
         const int64_t ncl = (int64_t)max(hx - lx + 1, 0) * max(hy - ly + 1, 0) * max(hz - lz + 1, 0);
         if (ncl > (int64_t)g.max_box_cells) break;
         if (tau >= 0.0f) {
@@ -105,6 +105,7 @@ __device__ int nearest_within(const Grid& g, float px, float py, float pz, float
     uint32_t bpos = 0u;
     for (int64_t i = 0; i < g.m; ++i) {
         const float4 q = __ldg(&g.pts[i]);
+        if (g.windowed && !in_window(g, q)) continue;
         const float d = sqdist_pinned(px, py, pz, q.x, q.y, q.z);
         const u64 key = ((u64)__float_as_uint(d) << 32) | (u64)__float_as_uint(q.w);
         if (d <= max_d2 && key < best) {

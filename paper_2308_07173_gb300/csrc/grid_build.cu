@@ -635,6 +635,7 @@ pc_status pc_build_grid(const float* xyz, int64_t M, const pc_build_opts& opts, 
     g.rank = t->rank;
     g.status = t->status;
     g.stats = reinterpret_cast<unsigned long long*>(reinterpret_cast<char*>(t->status) + 32);
+    pc_clear_window(g);
     t->device_bytes = (int64_t)(sizeof(uint4) * t->table_cap + 2 * sizeof(float4) * M +
                                 sizeof(u64) * U + sizeof(uint32_t) * (U + 1) + 64 +
                                 2 * sizeof(uint32_t) * nwords);

@@ -1,0 +1,824 @@
+// The search and covariance kernels, shared by knn_cov.cu (whole-map
+// searches) and knn_window.cu (searches restricted to a window, WIN = true):
+// each translation unit instantiates one window variant, so the whole-map
+// kernels carry no window code and the two compile in parallel.
+#pragma once
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+
+#include "pc_device.cuh"
+#include "pc_internal.h"
+#include "pc_search.cuh"
+
+using namespace pcdev;
+
+namespace {
+
+typedef unsigned long long u64;
+
+__device__ __forceinline__ u64 umin64(u64 a, u64 b) { return a < b ? a : b; }
+__device__ __forceinline__ u64 umax64(u64 a, u64 b) { return a < b ? b : a; }
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+// Bitonic sort of one key per lane into DESCENDING lane order.
+__device__ __forceinline__ u64 sort32_desc(u64 x, int lane) {
+#pragma unroll
+    for (int size = 2; size <= 32; size <<= 1) {
+#pragma unroll
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            u64 y = __shfl_xor_sync(FULL, x, stride);
+            bool desc_block = (lane & size) == 0;  // all lanes at size 32
+            bool lower = (lane & stride) == 0;
+            x = (lower == desc_block) ? umax64(x, y) : umin64(x, y);
+        }
+    }
+    return x;
+}
+
+// Bitonic merge of a bitonic lane sequence into ASCENDING lane order.
+__device__ __forceinline__ u64 merge32_asc(u64 x, int lane) {
+#pragma unroll
+    for (int stride = 16; stride > 0; stride >>= 1) {
+        u64 y = __shfl_xor_sync(FULL, x, stride);
+        x = ((lane & stride) == 0) ? umin64(x, y) : umax64(x, y);
+    }
+    return x;
+}
+
+template <int SLOTS>
+struct SearchState {
+    u64 L[SLOTS];  // lane l: rank l (slot 0) and rank 32 + l (slot 1)
+    u64 kth;       // warp-uniform: the rank k-1 key, EMPTY_KEY until k exist
+    int npend;     // warp-uniform: survivors staged in shared memory
+};
+
+template <int SLOTS>
+__device__ __forceinline__ void state_reset(SearchState<SLOTS>& S) {
+#pragma unroll
+    for (int s = 0; s < SLOTS; ++s) S.L[s] = EMPTY_KEY;
+    S.kth = EMPTY_KEY;
+    S.npend = 0;
+}
+
+template <int SLOTS>
+__device__ __forceinline__ u64 topk_rank(const SearchState<SLOTS>& S, int r) {
+    u64 v = (SLOTS == 2 && r >= 32) ? S.L[SLOTS - 1] : S.L[0];
+    return __shfl_sync(FULL, v, r & 31);
+}
+
+// Merge 32 staged keys (one per lane, any order) into the sorted top list.
+// A ascending + B descending -> min(A, B) is bitonic and holds the smallest
+// |A| of A u B; for two slots the 64-list [L0, min(L1, c)] is bitonic.
+template <int SLOTS>
+__device__ __forceinline__ void topk_merge(SearchState<SLOTS>& S, u64 c, int k, int lane) {
+    c = sort32_desc(c, lane);
+    if (SLOTS == 1) {
+        S.L[0] = merge32_asc(umin64(S.L[0], c), lane);
+    } else {
+        u64 b = umin64(S.L[SLOTS - 1], c);
+        u64 lo = umin64(S.L[0], b), hi = umax64(S.L[0], b);
+        S.L[0] = merge32_asc(lo, lane);
+        S.L[SLOTS - 1] = merge32_asc(hi, lane);
+    }
+    S.kth = topk_rank(S, k - 1);
+}
+
+template <int SLOTS>
+__device__ __forceinline__ void offer(SearchState<SLOTS>& S, bool pass, u64 key, u64* pend, int k,
+                                      int lane) {
+    unsigned m = __ballot_sync(FULL, pass);
+    if (m == 0u) return;
+    if (pass) pend[S.npend + __popc(m & lanemask_lt())] = key;
+    S.npend += __popc(m);
+    __syncwarp();
+    if (S.npend >= 32) {
+        topk_merge(S, pend[lane], k, lane);
+        __syncwarp();
+        const int rest = S.npend - 32;
+        if (lane < rest) pend[lane] = pend[32 + lane];
+        __syncwarp();
+        S.npend = rest;
+    }
+}
+
+template <int SLOTS>
+__device__ __forceinline__ void flush(SearchState<SLOTS>& S, u64* pend, int k, int lane) {
+    if (S.npend > 0) {
+        u64 c = lane < S.npend ? pend[lane] : EMPTY_KEY;
+        topk_merge(S, c, k, lane);
+        S.npend = 0;
+    }
+    __syncwarp();
+}
+
+// One pass over up to 32 point ranges (one per lane): every point becomes a
+// candidate, 32 per step, each lane finding its owning range by a binary
+// search over the warp's exclusive prefix of counts.
+template <int SLOTS>
+__device__ __forceinline__ void scan_ranges(const Grid& g, float qx, float qy, float qz,
+                                            uint32_t start, uint32_t cnt, float tau,
+                                            SearchState<SLOTS>& S, u64* pend, int k, int lane) {
+    uint32_t incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t t = __shfl_up_sync(FULL, incl, o);
+        if (lane >= o) incl += t;
+    }
+    const uint32_t total = __shfl_sync(FULL, incl, 31);
+    const uint32_t excl = incl - cnt;
+    for (uint32_t cb = 0; cb < total; cb += 32) {
+        const uint32_t t = cb + lane;
+        int j = 0;
+#pragma unroll
+        for (int s = 16; s >= 1; s >>= 1) {
+            uint32_t e = __shfl_sync(FULL, excl, j + s);
+            if (e <= t) j += s;
+        }
+        const uint32_t st = __shfl_sync(FULL, start, j);
+        const uint32_t ej = __shfl_sync(FULL, excl, j);
+        bool pass = false;
+        u64 key = EMPTY_KEY;
+        if (t < total) {
+            const float4 p = __ldg(&g.pts[st + (t - ej)]);
+            const float d2 = sqdist_pinned(qx, qy, qz, p.x, p.y, p.z);
+            key = ((u64)__float_as_uint(d2) << 32) | (u64)__float_as_uint(p.w);
+            pass = (d2 <= tau) && (key < S.kth) && (!g.windowed || in_window(g, p));
+        }
+        offer(S, pass, key, pend, k, lane);
+    }
+}
+
+// Lower bound on the binary32 d2 from q to any point of cell (cx, cy, cz);
+// same margin argument as certified_tau.
+__device__ __forceinline__ float cell_lower_bound2(const Grid& g, float qx, float qy, float qz,
+                                                   int cx, int cy, int cz) {
+    float qm = fmaxf(fabsf(qx), fmaxf(fabsf(qy), fabsf(qz)));
+    int cm = max(cx, max(cy, cz)) + 1;
+    float eta = 0x1p-20f * (g.coord_scale + qm + (float)cm * g.h);
+    float s = 0.0f;
+    {
+        float lo = g.ox + (float)cx * g.h, hi = g.ox + (float)(cx + 1) * g.h;
+        float d = fmaxf(fmaxf(lo - qx, qx - hi), 0.0f) - eta;
+        if (d > 0.0f) s = s + d * d;
+    }
+    {
+        float lo = g.oy + (float)cy * g.h, hi = g.oy + (float)(cy + 1) * g.h;
+        float d = fmaxf(fmaxf(lo - qy, qy - hi), 0.0f) - eta;
+        if (d > 0.0f) s = s + d * d;
+    }
+    {
+        float lo = g.oz + (float)cz * g.h, hi = g.oz + (float)(cz + 1) * g.h;
+        float d = fmaxf(fmaxf(lo - qz, qz - hi), 0.0f) - eta;
+        if (d > 0.0f) s = s + d * d;
+    }
+    return s * (1.0f - 0x1p-20f);
+}
+
+template <int SLOTS>
+__device__ void scan_box(const Grid& g, float qx, float qy, float qz, int lx, int ly, int lz,
+                         int ex, int ey, int ez, float tau, SearchState<SLOTS>& S, u64* pend,
+                         int k, int lane) {
+    const int ncl = ex * ey * ez;
+    for (int base = 0; base < ncl; base += 32) {
+        const int c = base + lane;
+        uint32_t start = 0u, cnt = 0u;
+        if (c < ncl) {
+            const int cx = lx + c % ex;
+            const int r = c / ex;
+            const int cy = ly + r % ey;
+            const int cz = lz + r / ey;
+            const uint2 v = lookup_cell(g, pack_key(cx, cy, cz, g.bx, g.by));
+            start = v.x;
+            cnt = v.y;
+        }
+        scan_ranges(g, qx, qy, qz, start, cnt, tau, S, pend, k, lane);
+    }
+}
+
+template <int SLOTS>
+__device__ void scan_all_cells(const Grid& g, float qx, float qy, float qz, SearchState<SLOTS>& S,
+                               u64* pend, int k, int lane) {
+    const u64 mx = (1ull << g.bx) - 1ull, my = (1ull << g.by) - 1ull;
+    for (int64_t ub = 0; ub < g.ncells; ub += 32) {
+        const int64_t u = ub + lane;
+        uint32_t start = 0u, cnt = 0u;
+        if (u < g.ncells) {
+            const u64 key = g.cell_keys[u];
+            const int cx = (int)(key & mx), cy = (int)((key >> g.bx) & my),
+                      cz = (int)(key >> (g.bx + g.by));
+            const float lb2 = cell_lower_bound2(g, qx, qy, qz, cx, cy, cz);
+            const float kd = S.kth == EMPTY_KEY ? INFINITY : __uint_as_float((uint32_t)(S.kth >> 32));
+            const bool win = cx >= g.wlx && cx <= g.whx && cy >= g.wly && cy <= g.why &&
+                             cz >= g.wlz && cz <= g.whz;
+            if (win && lb2 <= kd) {
+                start = g.cell_start[u];
+                cnt = g.cell_start[u + 1] - start;
+            }
+        }
+        scan_ranges(g, qx, qy, qz, start, cnt, INFINITY, S, pend, k, lane);
+    }
+}
+
+// Exact k nearest neighbours of one query (warp-uniform control flow).
+// Returns SEARCH_OK, SEARCH_LIMIT (max_box_cells reached with exhaustive =
+// 0) or SEARCH_SHORT (the exhaustive scan found fewer than k points: the
+// window holds fewer than k).
+constexpr int SEARCH_OK = 0, SEARCH_LIMIT = 1, SEARCH_SHORT = 2;
+template <int SLOTS>
+__device__ int knn_search(const Grid& g, float qx, float qy, float qz, int k, float& rho,
+                           SearchState<SLOTS>& S, u64* pend, int lane) {
+    for (int attempt = 0; attempt < 40; ++attempt) {
+        const int lx = cell_of(__fsub_rn(qx, rho), g.ox, g.inv_h);
+        const int hx = cell_of(__fadd_rn(qx, rho), g.ox, g.inv_h);
+        const int ly = cell_of(__fsub_rn(qy, rho), g.oy, g.inv_h);
+        const int hy = cell_of(__fadd_rn(qy, rho), g.oy, g.inv_h);
+        const int lz = cell_of(__fsub_rn(qz, rho), g.oz, g.inv_h);
+        const int hz = cell_of(__fadd_rn(qz, rho), g.oz, g.inv_h);
+        const float tau = certified_tau(g, qx, qy, qz, lx, hx, ly, hy, lz, hz);
+        const int cxl = max(lx, g.wlx), cxh = min(hx, g.whx);
+        const int cyl = max(ly, g.wly), cyh = min(hy, g.why);
+        const int czl = max(lz, g.wlz), czh = min(hz, g.whz);
+        const int64_t ex = max(cxh - cxl + 1, 0), ey = max(cyh - cyl + 1, 0),
+                      ez = max(czh - czl + 1, 0);
+        const int64_t ncl = ex * ey * ez;
+        if (ncl > (int64_t)g.max_box_cells) break;
+        state_reset(S);
+        if (ncl > 0)
+            scan_box(g, qx, qy, qz, cxl, cyl, czl, (int)ex, (int)ey, (int)ez, tau, S, pend, k,
+                     lane);
+        flush(S, pend, k, lane);
+        if (S.kth != EMPTY_KEY) return SEARCH_OK;
+        int found = 0;
+#pragma unroll
+        for (int s = 0; s < SLOTS; ++s) found += __popc(__ballot_sync(FULL, S.L[s] != EMPTY_KEY));
+        float f = 1.3f * sqrtf((float)k / (float)max(found, 1));
+        f = fminf(fmaxf(f, 1.5f), 4.0f);
+        rho = fminf(fmaxf(rho, 1e-3f * g.h) * f, 1e30f);
+    }
+    if (!g.exhaustive) return SEARCH_LIMIT;
+    if (lane == 0) atomicAdd(&g.stats[2], 1ull);
+    state_reset(S);
+    scan_all_cells(g, qx, qy, qz, S, pend, k, lane);
+    flush(S, pend, k, lane);
+    return S.kth != EMPTY_KEY ? SEARCH_OK : SEARCH_SHORT;
+}
+
+// ---------------------------------------------------------------- covariance
+
+// One Jacobi rotation in the (p,q) plane that zeroes a_pq of a symmetric
+// matrix (r is the remaining index): with theta = (a_qq - a_pp) / (2 a_pq)
+// and t the smaller root of t^2 + 2 t theta - 1 = 0, c = 1/sqrt(1+t^2),
+// s = t c, the diagonal moves by -+ t a_pq and the r-row and the
+// eigenvector columns p, q rotate by (c, s) (Golub & Van Loan, sec. 8.5).
+__host__ __device__ __forceinline__ void jacobi_rotate(float& app, float& aqq, float& apq, float& arp,
+                                              float& arq, float& v0p, float& v0q, float& v1p,
+                                              float& v1q, float& v2p, float& v2q) {
+    if (apq == 0.0f) return;
+    const float theta = (aqq - app) / (2.0f * apq);
+    const float at = fabsf(theta);
+    const float t = at > 1e18f ? 0.5f / theta
+                               : copysignf(1.0f, theta) / (at + sqrtf(theta * theta + 1.0f));
+    const float c = 1.0f / sqrtf(t * t + 1.0f);
+    const float sn = t * c;
+    app = app - t * apq;
+    aqq = aqq + t * apq;
+    apq = 0.0f;
+    float x = arp, y = arq;
+    arp = c * x - sn * y;
+    arq = sn * x + c * y;
+    x = v0p; y = v0q; v0p = c * x - sn * y; v0q = sn * x + c * y;
+    x = v1p; y = v1q; v1p = c * x - sn * y; v1q = sn * x + c * y;
+    x = v2p; y = v2q; v2p = c * x - sn * y; v2q = sn * x + c * y;
+}
+
+// Unit eigenvector of the smallest eigenvalue of a symmetric 3x3 matrix, by
+// cyclic Jacobi sweeps in binary32 (pairs (0,1), (0,2), (1,2) in that order,
+// at most 8 sweeps, stopping once the off-diagonal mass is at rounding
+// level).  Its eigenvector error is ~ u ||C|| / (lambda2 - lambda3), the
+// perturbation bound itself.  The trigonometric closed form for 3x3
+// eigenvalues was tried first and dropped: in binary32 its acos step loses
+// accuracy to ~sqrt(u) when two eigenvalues nearly coincide (isotropic
+// planar patches), which the 1e-5 covariance bar exposes.  The matrix is
+// scaled by an exact power of two first; a zero matrix gives e_z.
+__host__ __device__ float3 min_eigvec(float a00, float a01, float a02, float a11, float a12, float a22) {
+    const float amax = fmaxf(fmaxf(fabsf(a00), fabsf(a11)),
+                             fmaxf(fabsf(a22), fmaxf(fmaxf(fabsf(a01), fabsf(a02)), fabsf(a12))));
+    if (!(amax > 0.0f) || !isfinite(amax)) return make_float3(0.0f, 0.0f, 1.0f);
+    int e;
+    frexpf(amax, &e);
+    const float sc = ldexpf(1.0f, -e);
+    a00 *= sc; a01 *= sc; a02 *= sc; a11 *= sc; a12 *= sc; a22 *= sc;
+    float v00 = 1.0f, v01 = 0.0f, v02 = 0.0f;
+    float v10 = 0.0f, v11 = 1.0f, v12 = 0.0f;
+    float v20 = 0.0f, v21 = 0.0f, v22 = 1.0f;
+    for (int sweep = 0; sweep < 8; ++sweep) {
+        const float off = a01 * a01 + a02 * a02 + a12 * a12;
+        const float dia = a00 * a00 + a11 * a11 + a22 * a22;
+        if (!(off > 1e-15f * dia)) break;
+        jacobi_rotate(a00, a11, a01, a02, a12, v00, v01, v10, v11, v20, v21);  // (0,1), r = 2
+        jacobi_rotate(a00, a22, a02, a01, a12, v00, v02, v10, v12, v20, v22);  // (0,2), r = 1
+        jacobi_rotate(a11, a22, a12, a01, a02, v01, v02, v11, v12, v21, v22);  // (1,2), r = 0
+    }
+    float3 n = make_float3(v00, v10, v20);
+    float lmin = a00;
+    if (a11 < lmin) { lmin = a11; n = make_float3(v01, v11, v21); }
+    if (a22 < lmin) { n = make_float3(v02, v12, v22); }
+    const float inv = 1.0f / sqrtf(n.x * n.x + n.y * n.y + n.z * n.z);
+    return make_float3(n.x * inv, n.y * inv, n.z * inv);
+}
+
+// Covariance of one neighbourhood (Sec. III-C1, C_i of Eq. 19) from its
+// points in rank order, get(j) for j = 0..k-1.  Two passes in binary32,
+// both shifted by the first (nearest) neighbour p0 so the sums stay small:
+// mean m of (p_j - p0), then the centred moments of (p_j - p0) - m, divided
+// by k.  Built with --fmad=false, so every + and * below is rounded once;
+// every caller runs this same code on the same values, so the fused kernel
+// and pc_cov agree bit for bit.
+template <typename G>
+__device__ __forceinline__ void cov_core(G&& get, int k, float eps, float* out) {
+    const float4 p0 = get(0);
+    float sx = 0.0f, sy = 0.0f, sz = 0.0f;
+    for (int j = 0; j < k; ++j) {
+        const float4 p = get(j);
+        sx = sx + (p.x - p0.x);
+        sy = sy + (p.y - p0.y);
+        sz = sz + (p.z - p0.z);
+    }
+    const float fk = (float)k;
+    const float mx = sx / fk, my = sy / fk, mz = sz / fk;
+    float cxx = 0.0f, cxy = 0.0f, cxz = 0.0f, cyy = 0.0f, cyz = 0.0f, czz = 0.0f;
+    for (int j = 0; j < k; ++j) {
+        const float4 p = get(j);
+        const float dx = (p.x - p0.x) - mx;
+        const float dy = (p.y - p0.y) - my;
+        const float dz = (p.z - p0.z) - mz;
+        cxx = __fmaf_rn(dx, dx, cxx);
+        cxy = __fmaf_rn(dx, dy, cxy);
+        cxz = __fmaf_rn(dx, dz, cxz);
+        cyy = __fmaf_rn(dy, dy, cyy);
+        cyz = __fmaf_rn(dy, dz, cyz);
+        czz = __fmaf_rn(dz, dz, czz);
+    }
+    cxx = cxx / fk; cxy = cxy / fk; cxz = cxz / fk;
+    cyy = cyy / fk; cyz = cyz / fk; czz = czz / fk;
+    if (eps < 0.0f) {
+        out[0] = cxx; out[1] = cxy; out[2] = cxz; out[3] = cyy; out[4] = cyz; out[5] = czz;
+        return;
+    }
+    const float3 n = min_eigvec(cxx, cxy, cxz, cyy, cyz, czz);
+    const float f = 1.0f - eps;
+    out[0] = 1.0f - f * n.x * n.x;
+    out[1] = -f * n.x * n.y;
+    out[2] = -f * n.x * n.z;
+    out[3] = 1.0f - f * n.y * n.y;
+    out[4] = -f * n.y * n.z;
+    out[5] = 1.0f - f * n.z * n.z;
+}
+
+__device__ __forceinline__ void nan_row(float* out) {
+    const float nan = __int_as_float(0x7fc00000);
+    for (int e = 0; e < 6; ++e) out[e] = nan;
+}
+
+// Covariance of the neighbourhood row nb[0], nb[st], ..., nb[(k-1) st]
+// (caller indices, read from the caller-order copy).  `check`: validate
+// every index (pc_cov); otherwise a leading -1 marks an unanswered row.
+__device__ void cov_row(const Grid& g, const int32_t* nb, int st, int k, float eps, float* out,
+                        bool check) {
+    bool bad = nb[0] < 0;
+    if (check) {
+        bool oob = false;
+        for (int j = 0; j < k; ++j) oob |= (nb[j * st] < 0) || ((int64_t)nb[j * st] >= g.m);
+        if (oob) atomicOr(g.status, ST_BAD_INDEX);
+        bad = oob;
+    }
+    if (bad) {
+        nan_row(out);
+        return;
+    }
+    cov_core([&](int j) { return __ldg(&g.xyz[nb[j * st]]); }, k, eps, out);
+}
+
+// ---------------------------------------------------------------- tiles
+struct TileArgs {
+    int k;
+    float eps;
+    float rho_scale;
+    int last_first;  // issue tiles from the end of the query array
+};
+
+// Per-warp shared memory: 64 staged survivor keys of the warp-cooperative
+// search, then the lane path's survivor lists: 32 slots x 32 lanes of
+// positions into pts ([slot][lane], so a slot is one 128-byte row).
+// Search modes: 0 = lane path with room for 32 survivors (k <= 24),
+// 1 = lane path with room for 64 (k <= 32), 2 = warp path only (k > 32).
+__host__ __device__ __forceinline__ int lane_cap(int mode) { return mode == 0 ? 32 : mode == 1 ? 64 : 0; }
+__host__ __device__ __forceinline__ int search_mode(int k) { return k <= 24 ? 0 : (k <= 32 ? 1 : 2); }
+__host__ __device__ __forceinline__ size_t warp_smem_bytes(int mode) {
+    return 64 * sizeof(u64) + (size_t)lane_cap(mode) * 32 * sizeof(uint32_t);
+}
+
+__device__ __forceinline__ void cas32(uint32_t& a, uint32_t& b) {
+    const uint32_t lo = min(a, b), hi = max(a, b);
+    a = lo;
+    b = hi;
+}
+
+// Bitonic sort network over the first NN registers, ascending.
+template <int NN, int CAP>
+__device__ __forceinline__ void sort_regs(uint32_t (&K)[CAP]) {
+#pragma unroll
+    for (int size = 2; size <= NN; size <<= 1)
+#pragma unroll
+        for (int stride = size >> 1; stride > 0; stride >>= 1)
+#pragma unroll
+            for (int i = 0; i < NN; ++i) {
+                const int j = i ^ stride;
+                if (j > i) {
+                    if ((i & size) == 0) cas32(K[i], K[j]);
+                    else cas32(K[j], K[i]);
+                }
+            }
+}
+
+// Trial radii of the lane path, as multiples of the starting radius: a
+// geometric ladder with ratio 1.1 (so the count at the chosen radius is at
+// most ~1.2x the smallest count that reaches k on a surface).
+constexpr int NRAD = 8;
+__device__ __forceinline__ float rad_mul(int j) {
+    return j == 0 ? 0.75f : j == 1 ? 0.83f : j == 2 ? 0.91f : j == 3 ? 1.0f
+         : j == 4 ? 1.1f : j == 5 ? 1.21f : j == 6 ? 1.33f : 1.46f;
+}
+
+// (d2, index) key of the survivor in a lane's slot, recomputed from pts.
+__device__ __forceinline__ u64 slot_key(const Grid& g, const uint32_t* posl, int slot, int lane,
+                                        float qx, float qy, float qz) {
+    const float4 p = __ldg(&g.pts[posl[slot * 32 + lane]]);
+    const float d = sqdist_pinned(qx, qy, qz, p.x, p.y, p.z);
+    return ((u64)__float_as_uint(d) << 32) | (u64)__float_as_uint(p.w);
+}
+
+// k <= 32: one query per lane.  Pass 1 counts, for each trial radius
+// r_j = m_j rho0, the target points with d2 <= t_j = min(r_j^2, tau), tau
+// certified for the box around the largest radius; the smallest t_j that
+// holds >= k points (and at most 32) is exact by the same argument as the
+// warp search: every point with d2 <= t_j lies in the box, so the k
+// smallest of those are the k smallest overall.  Pass 2 collects their
+// positions in the lane's shared-memory list.  They are ordered by a
+// register bitonic network on 32-bit keys (d2 bits << 1 with the low five
+// bits replaced by the slot), which orders d2 to within 16 ulps; any run of
+// neighbours left in the same 16-ulp bucket is then put in exact (d2,
+// index) order by bubble passes on the full keys.  Lanes whose query needs
+// a wider radius, more than 32 survivors or a bigger box are finished by
+// the warp-cooperative search, one query at a time.
+template <int CAP, bool COV, bool WIN>
+__device__ void lane_tile(const Grid& g, const float* __restrict__ q, int64_t n0, int cnt,
+                          const TileArgs& a, float rho0, int32_t* __restrict__ idx,
+                          float* __restrict__ d2, float* __restrict__ cov, u64* pend,
+                          uint32_t* posl, int lane) {
+    const int k = a.k;
+    const bool active = lane < cnt;
+    const int64_t n = n0 + lane;
+    float qx = 0.0f, qy = 0.0f, qz = 0.0f;
+    if (active) {
+        qx = __ldg(q + 3 * n);
+        qy = __ldg(q + 3 * n + 1);
+        qz = __ldg(q + 3 * n + 2);
+    }
+    const bool finite = active && isfinite(qx) && isfinite(qy) && isfinite(qz);
+    bool fallback = false;
+    int m = 0;
+    float thr = -1.0f;
+    int lx = 0, hx = -1, ly = 0, hy = -1, lz = 0, hz = -1;
+    float eta = 0.0f;
+    // Up to two lane-parallel attempts: a lane whose largest trial radius
+    // held fewer than k points retries with the radii x1.8, one whose
+    // smallest held more than CAP retries with them x0.7; only lanes that
+    // still fail go to the warp search.
+    float rho = rho0;
+    bool todo = finite;
+    for (int attempt = 0; attempt < 2 && __any_sync(FULL, todo); ++attempt) {
+        if (todo) {
+            todo = false;
+            const float rmax = rho * rad_mul(NRAD - 1);
+            const int ulx = cell_of(__fsub_rn(qx, rmax), g.ox, g.inv_h);
+            const int uhx = cell_of(__fadd_rn(qx, rmax), g.ox, g.inv_h);
+            const int uly = cell_of(__fsub_rn(qy, rmax), g.oy, g.inv_h);
+            const int uhy = cell_of(__fadd_rn(qy, rmax), g.oy, g.inv_h);
+            const int ulz = cell_of(__fsub_rn(qz, rmax), g.oz, g.inv_h);
+            const int uhz = cell_of(__fadd_rn(qz, rmax), g.oz, g.inv_h);
+            const float tau = certified_tau(g, qx, qy, qz, ulx, uhx, uly, uhy, ulz, uhz);
+            {
+                const int cm = max(max(max(abs(ulx), abs(uhx + 1)), max(abs(uly), abs(uhy + 1))),
+                                   max(abs(ulz), abs(uhz + 1)));
+                const float qm = fmaxf(fabsf(qx), fmaxf(fabsf(qy), fabsf(qz)));
+                eta = 0x1p-20f * (g.coord_scale + qm + (float)cm * g.h);
+            }
+            lx = max(ulx, WIN ? g.wlx : 0); hx = min(uhx, WIN ? g.whx : g.dimx - 1);
+            ly = max(uly, WIN ? g.wly : 0); hy = min(uhy, WIN ? g.why : g.dimy - 1);
+            lz = max(ulz, WIN ? g.wlz : 0); hz = min(uhz, WIN ? g.whz : g.dimz - 1);
+            const int64_t ncl = (int64_t)max(hx - lx + 1, 0) * max(hy - ly + 1, 0) * max(hz - lz + 1, 0);
+            const int64_t nrows = (int64_t)max(hy - ly + 1, 0) * max(hz - lz + 1, 0);
+            fallback = false;
+            if (tau < 0.0f || ncl > 4096 || nrows > 256 || (!g.occ && ncl > 256)) {
+                fallback = true;
+            } else {
+                float t[NRAD];
+                int c[NRAD];
+#pragma unroll
+                for (int j = 0; j < NRAD; ++j) {
+                    const float r = rho * rad_mul(j);
+                    t[j] = fminf(r * r, tau);
+                    c[j] = 0;
+                }
+                auto count = [&](uint32_t, const float4 p) {
+                    const float d = sqdist_pinned(qx, qy, qz, p.x, p.y, p.z);
+#pragma unroll
+                    for (int j = 0; j < NRAD; ++j) c[j] += d <= t[j] ? 1 : 0;
+                };
+                if (g.occ) for_rows<WIN>(g, qx, qy, qz, lx, hx, ly, hy, lz, hz, eta, t[NRAD - 1], count);
+                else for_box_points<WIN>(g, qx, qy, qz, lx, hx, ly, hy, lz, hz, eta, t[NRAD - 1], count);
+                int js = -1;
+#pragma unroll
+                for (int j = NRAD - 1; j >= 0; --j)
+                    if (c[j] >= k) js = j;
+                int cj = 0;
+                float tj = -1.0f;
+#pragma unroll
+                for (int j = 0; j < NRAD; ++j)
+                    if (j == js) { cj = c[j]; tj = t[j]; }
+                if (js < 0 || cj > CAP) {
+                    fallback = true;
+                    // too few within the certified radii: widen; too many: narrow
+                    // (unless the certified radius, not the trial radius, was short)
+                    const bool widen = js < 0;
+                    if (!(widen && t[NRAD - 1] >= tau)) {
+                        todo = true;
+                        rho = widen ? rho * 1.8f : rho * 0.7f;
+                    }
+                } else {
+                    m = cj;
+                    thr = tj;
+                }
+            }
+        }
+    }
+    if (m > 0) {
+        int w = 0;
+        auto collect = [&](uint32_t pos, const float4 p) {
+            const float d = sqdist_pinned(qx, qy, qz, p.x, p.y, p.z);
+            if (d <= thr && w < CAP) {
+                posl[w * 32 + lane] = pos;
+                ++w;
+            }
+        };
+        if (g.occ) for_rows<WIN>(g, qx, qy, qz, lx, hx, ly, hy, lz, hz, eta, thr, collect);
+        else for_box_points<WIN>(g, qx, qy, qz, lx, hx, ly, hy, lz, hz, eta, thr, collect);
+    }
+    __syncwarp();
+    uint32_t K[CAP];
+#pragma unroll
+    for (int s = 0; s < CAP; ++s) {
+        uint32_t key = 0xffffffffu;
+        if (s < m) {
+            const float4 p = __ldg(&g.pts[posl[s * 32 + lane]]);
+            const float d = sqdist_pinned(qx, qy, qz, p.x, p.y, p.z);
+            key = ((__float_as_uint(d) << 1) & ~(uint32_t)(CAP - 1)) | (uint32_t)s;
+        }
+        K[s] = key;
+    }
+    const unsigned mmax = __reduce_max_sync(FULL, (unsigned)m);
+    if (mmax <= 16u) sort_regs<16>(K);
+    else if (CAP == 32 || mmax <= 32u) sort_regs<32>(K);
+    else sort_regs<CAP>(K);
+    bool amb = false;
+#pragma unroll
+    for (int r = 0; r + 1 < CAP; ++r) amb |= (r + 1 < m) && ((K[r] ^ K[r + 1]) < (uint32_t)CAP);
+    for (int pass = 0; amb && pass < CAP; ++pass) {
+        bool swapped = false;
+#pragma unroll
+        for (int r = 0; r + 1 < CAP; ++r) {
+            if (r + 1 < m && ((K[r] ^ K[r + 1]) < (uint32_t)CAP)) {
+                const u64 ka = slot_key(g, posl, (int)(K[r] & (CAP - 1)), lane, qx, qy, qz);
+                const u64 kb = slot_key(g, posl, (int)(K[r + 1] & (CAP - 1)), lane, qx, qy, qz);
+                if (kb < ka) {
+                    const uint32_t tmp = K[r];
+                    K[r] = K[r + 1];
+                    K[r + 1] = tmp;
+                    swapped = true;
+                }
+            }
+        }
+        amb = swapped;
+    }
+    if (m > 0) {
+        // rank-ordered positions, rewritten in place into the list's first k slots
+        uint32_t P[32];
+#pragma unroll
+        for (int r = 0; r < 32; ++r)
+            if (r < k) P[r] = posl[(K[r] & (CAP - 1)) * 32 + lane];
+#pragma unroll
+        for (int r = 0; r < 32; ++r)
+            if (r < k) {
+                posl[r * 32 + lane] = P[r];
+                const float4 p = __ldg(&g.pts[P[r]]);
+                idx[n * k + r] = (int32_t)__float_as_uint(p.w);
+                d2[n * k + r] = sqdist_pinned(qx, qy, qz, p.x, p.y, p.z);
+            }
+    } else if (active && !finite) {
+        for (int r = 0; r < k; ++r) {
+            idx[n * k + r] = -1;
+            d2[n * k + r] = INFINITY;
+        }
+        atomicOr(g.status, ST_NONFINITE);
+    }
+    unsigned fb = __ballot_sync(FULL, fallback);
+    if (lane == 0) {
+        atomicAdd(&g.stats[0], (unsigned long long)cnt);
+        if (fb) atomicAdd(&g.stats[1], (unsigned long long)__popc(fb));
+    }
+    while (fb) {
+        const int f = __ffs(fb) - 1;
+        fb &= fb - 1u;
+        const float fx = __shfl_sync(FULL, qx, f), fy = __shfl_sync(FULL, qy, f),
+                    fz = __shfl_sync(FULL, qz, f);
+        float rho = rho0 * rad_mul(NRAD - 1);
+        SearchState<1> S;
+        state_reset(S);
+        const int sr = knn_search<1>(g, fx, fy, fz, k, rho, S, pend, lane);
+        const bool ok = sr == SEARCH_OK;
+        if (!ok && lane == 0) atomicOr(g.status, sr == SEARCH_SHORT ? ST_SHORT : ST_SEARCH_LIMIT);
+        const int64_t nf = n0 + f;
+        if (lane < k) {
+            idx[nf * k + lane] = ok ? (int32_t)(uint32_t)S.L[0] : -1;
+            d2[nf * k + lane] = ok ? __uint_as_float((uint32_t)(S.L[0] >> 32)) : INFINITY;
+        }
+    }
+    if (COV && cov != nullptr) {
+        __syncwarp();  // orders the idx rows written by other lanes
+        if (m > 0)  // neighbours straight from the cell-sorted copy, in rank order
+            cov_core([&](int j) { return __ldg(&g.pts[posl[j * 32 + lane]]); }, k, a.eps, cov + 6 * n);
+        else if (active)
+            cov_row(g, idx + n * k, 1, k, a.eps, cov + 6 * n, false);
+    }
+    __syncwarp();
+}
+
+// k > 32: the warp-cooperative search for each query of the tile in turn.
+template <bool COV>
+__device__ void warp_tile(const Grid& g, const float* __restrict__ q, int64_t n0, int cnt,
+                          const TileArgs& a, float rho0, int32_t* __restrict__ idx,
+                          float* __restrict__ d2, float* __restrict__ cov, u64* pend,
+                          int lane) {
+    const int k = a.k;
+    float rho = rho0;
+    if (lane == 0) {
+        atomicAdd(&g.stats[0], (unsigned long long)cnt);
+        atomicAdd(&g.stats[1], (unsigned long long)cnt);
+    }
+    for (int i = 0; i < cnt; ++i) {
+        const int64_t n = n0 + i;
+        const float qx = __ldg(q + 3 * n), qy = __ldg(q + 3 * n + 1), qz = __ldg(q + 3 * n + 2);
+        const bool finite = isfinite(qx) && isfinite(qy) && isfinite(qz);
+        SearchState<2> S;
+        state_reset(S);
+        int sr = SEARCH_LIMIT;
+        if (finite) sr = knn_search<2>(g, qx, qy, qz, k, rho, S, pend, lane);
+        const bool ok = finite && sr == SEARCH_OK;
+        if (!ok && lane == 0)
+            atomicOr(g.status, !finite ? ST_NONFINITE : sr == SEARCH_SHORT ? ST_SHORT : ST_SEARCH_LIMIT);
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+            const int r = s * 32 + lane;
+            if (r < k) {
+                const u64 key = S.L[s];
+                const int32_t oi = ok ? (int32_t)(uint32_t)key : -1;
+                idx[n * k + r] = oi;
+                d2[n * k + r] = ok ? __uint_as_float((uint32_t)(key >> 32)) : INFINITY;
+            }
+        }
+        if (ok) {
+            const float dk = __uint_as_float((uint32_t)(S.kth >> 32));
+            rho = fminf(fmaxf(sqrtf(dk) * 1.15f, 1e-2f * g.h), 1e30f);
+        }
+    }
+    if (COV && cov != nullptr) {
+        __syncwarp();
+        if (lane < cnt) cov_row(g, idx + (n0 + lane) * k, 1, k, a.eps, cov + 6 * (n0 + lane), false);
+        __syncwarp();
+    }
+}
+
+template <int MODE, bool COV, bool WIN>
+__device__ __forceinline__ void process_tile(const Grid& g, const float* __restrict__ q, int64_t n0,
+                                             int cnt, const TileArgs& a, float rho0,
+                                             int32_t* __restrict__ idx, float* __restrict__ d2,
+                                             float* __restrict__ cov, unsigned char* wsmem,
+                                             int lane) {
+    u64* pend = reinterpret_cast<u64*>(wsmem);
+    uint32_t* posl = reinterpret_cast<uint32_t*>(wsmem + 64 * sizeof(u64));
+    if (MODE == 0)
+        lane_tile<32, COV, WIN>(g, q, n0, cnt, a, rho0, idx, d2, cov, pend, posl, lane);
+    else if (MODE == 1)
+        lane_tile<64, COV, WIN>(g, q, n0, cnt, a, rho0, idx, d2, cov, pend, posl, lane);
+    else
+        warp_tile<COV>(g, q, n0, cnt, a, rho0, idx, d2, cov, pend, lane);
+}
+
+template <int MODE, bool COV, bool WIN>
+__global__ void __launch_bounds__(256, 2) k_knn(Grid g, const float* __restrict__ q, int64_t N,
+                                             int tile, TileArgs a, float rho0,
+                                             int32_t* __restrict__ idx, float* __restrict__ d2,
+                                             float* __restrict__ cov) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nwarps = blockDim.x >> 5;
+    // Tiles are issued last-first.  A spinning LiDAR scan stored ring by ring
+    // with rising elevation ends with its farthest, sparsest points, whose
+    // tiles cost the most; starting them first lets the cheap near-range
+    // tiles fill the end of the launch.  (The order never changes a result.)
+    const int64_t tiles = (N + tile - 1) / tile;
+    const int64_t w = (int64_t)blockIdx.x * nwarps + warp;
+    if (w >= tiles) return;
+    const int64_t t = a.last_first ? tiles - 1 - w : w;
+    const int64_t n0 = t * tile;
+    const int cnt = (int)min((int64_t)tile, N - n0);
+    process_tile<MODE, COV, WIN>(g, q, n0, cnt, a, rho0, idx, d2, cov,
+                            smem + (size_t)warp * warp_smem_bytes(MODE), lane);
+}
+
+// Batched form: one persistent launch; warps pull (scan, tile) items from a
+// device counter over the scans' prefix-summed tile table.
+template <int MODE, bool COV, bool WIN>
+__global__ void __launch_bounds__(256, 2) k_knn_batch(Grid g, const ScanDesc* __restrict__ scans,
+                                                   int nscans, int64_t total_tiles, int tile,
+                                                   TileArgs a, float rho0,
+                                                   unsigned long long* counter) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    unsigned char* wsmem = smem + (size_t)warp * warp_smem_bytes(MODE);
+    for (;;) {
+        unsigned long long item = 0;
+        if (lane == 0) item = atomicAdd(counter, 1ull);
+        item = __shfl_sync(FULL, item, 0);
+        if ((int64_t)item >= total_tiles) break;
+        int lo = 0, hi = nscans - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (scans[mid].tile0 <= (int64_t)item) lo = mid; else hi = mid - 1;
+        }
+        const ScanDesc sd = scans[lo];
+        const int64_t n0 = ((int64_t)item - sd.tile0) * tile;
+        const int cnt = (int)min((int64_t)tile, sd.n - n0);
+        process_tile<MODE, COV, WIN>(g, sd.q, n0, cnt, a, rho0, sd.idx, sd.d2, sd.cov, wsmem, lane);
+    }
+}
+
+__global__ void k_cov(Grid g, const int32_t* __restrict__ idx, int64_t N, int k, float eps,
+                      float* __restrict__ cov) {
+    const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    cov_row(g, idx + n * k, 1, k, eps, cov + 6 * n, true);
+}
+
+template <typename K>
+cudaError_t allow_smem(K kern) {
+    return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+}
+
+// The search kernel for (mode, covariance, batched) of this window variant.
+template <bool WIN>
+void* knn_kernel(int mode, bool with_cov, bool batch) {
+#define PC_PICK(M, C) (batch ? (void*)k_knn_batch<M, C, WIN> : (void*)k_knn<M, C, WIN>)
+    switch (mode * 2 + (with_cov ? 1 : 0)) {
+        case 0: return PC_PICK(0, false);
+        case 1: return PC_PICK(0, true);
+        case 2: return PC_PICK(1, false);
+        case 3: return PC_PICK(1, true);
+        case 4: return PC_PICK(2, false);
+        default: return PC_PICK(2, true);
+    }
+#undef PC_PICK
+}
+
+// Opts every search kernel of this window variant into large dynamic
+// shared memory.
+template <bool WIN>
+cudaError_t allow_all_smem() {
+    cudaError_t e = cudaSuccess;
+    for (int mode = 0; mode < 3; ++mode)
+        for (int c = 0; c < 2; ++c)
+            for (int b = 0; b < 2; ++b)
+                if ((e = allow_smem(knn_kernel<WIN>(mode, c != 0, b != 0))) != cudaSuccess) return e;
+    return cudaSuccess;
+}
+
+}  // namespace
+

@@ -99,7 +99,7 @@ extern "C" pc_status pc_batch_run_noalloc(pc_target t, const pc_scan* scans, int
                                     cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), st);
     if (e == cudaSuccess)
-        e = pc_launch_knn_batch(t, table_dev, n_scans, tiles, tile, warps, blocks, k, eps, any_cov,
+        e = pc_launch_knn_batch(t, t->g, table_dev, n_scans, tiles, tile, warps, blocks, k, eps, any_cov,
                                 pc_rho0(t, k), counter, st);
     return pc_from_cuda(e);
 }

@@ -81,6 +81,7 @@ pc_status read_and_clear_status(pc_target_s* t, cudaStream_t s) {
     if (st & pcdev::ST_NONFINITE) return PC_ERR_NONFINITE;
     if (st & pcdev::ST_SEARCH_LIMIT) return PC_ERR_SEARCH_LIMIT;
     if (st & pcdev::ST_BAD_INDEX) return PC_ERR_BAD_INDEX;
+    if (st & pcdev::ST_SHORT) return PC_ERR_K_GT_M;
     return PC_OK;
 }
 
@@ -382,6 +383,7 @@ pc_status pc_batch_plan(pc_target t, const pc_scan* scans, int n_scans, int k, f
     std::memset(b, 0, sizeof(*b));
     b->magic = PC_MAGIC_LIVE;
     b->t = t;
+    b->g = t->g;
     b->n_scans = n_scans;
     b->k = k;
     b->eps = eps;
@@ -429,7 +431,7 @@ pc_status pc_batch_run(pc_batch b, pc_stream s) {
     if (st == nullptr) {  // the legacy stream cannot be captured: launch directly
         cudaError_t e = cudaMemsetAsync(b->counter, 0, sizeof(unsigned long long), st);
         if (e == cudaSuccess)
-            e = pc_launch_knn_batch(b->t, b->scans_dev, b->n_scans, b->total_tiles, b->tile,
+            e = pc_launch_knn_batch(b->t, b->g, b->scans_dev, b->n_scans, b->total_tiles, b->tile,
                                     b->warps, b->blocks, b->k, b->eps, b->with_cov, rho0,
                                     b->counter, st);
         return pc_from_cuda(e);
@@ -442,7 +444,7 @@ pc_status pc_batch_run(pc_batch b, pc_stream s) {
         cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
         if (e != cudaSuccess) return pc_from_cuda(e);
         cudaError_t e1 = cudaMemsetAsync(b->counter, 0, sizeof(unsigned long long), st);
-        cudaError_t e2 = pc_launch_knn_batch(b->t, b->scans_dev, b->n_scans, b->total_tiles,
+        cudaError_t e2 = pc_launch_knn_batch(b->t, b->g, b->scans_dev, b->n_scans, b->total_tiles,
                                              b->tile, b->warps, b->blocks, b->k, b->eps,
                                              b->with_cov, rho0, b->counter, st);
         e = cudaStreamEndCapture(st, &b->graph);
@@ -512,7 +514,7 @@ pc_status pc_batch_run_scratch(pc_target t, const pc_scan* scans, int n_scans, i
                                     cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), st);
     if (e == cudaSuccess)
-        e = pc_launch_knn_batch(t, table, n_scans, tiles, tile, warps, blocks, k, eps, any_cov,
+        e = pc_launch_knn_batch(t, t->g, table, n_scans, tiles, tile, warps, blocks, k, eps, any_cov,
                                 pc_rho0(t, k), counter, st);
     return pc_from_cuda(e);
 }
@@ -526,6 +528,62 @@ void pc_batch_destroy(pc_batch b) {
     if (b->counter) cudaFree(b->counter);
     b->magic = PC_MAGIC_DEAD;
     delete b;
+}
+
+// The cell rule of the grid on the host (same binary32 operations as
+// pcdev::cell_of: a subtraction, a product, floor, clamp).
+static int host_cell_of(float v, float o, float inv_h) {
+    float t = (v - o) * inv_h;
+    t = std::floor(t);
+    t = std::fmin(std::fmax(t, -1073741824.0f), 1073741824.0f);
+    return (int)t;
+}
+
+pc_status pc_set_window(pc_target t, const pc_window* w) {
+    pc_status r = check_target(t);
+    if (r != PC_OK) return r;
+    pcdev::Grid& g = t->g;
+    if (!w) {
+        pc_clear_window(g);
+        return PC_OK;
+    }
+    for (int a = 0; a < 3; ++a)
+        if (std::isnan(w->lo[a]) || std::isnan(w->hi[a]) || !(w->lo[a] <= w->hi[a]))
+            return PC_ERR_INVALID_ARG;
+    const float o[3] = {g.ox, g.oy, g.oz};
+    const int dim[3] = {g.dimx, g.dimy, g.dimz};
+    int lo[3], hi[3];
+    for (int a = 0; a < 3; ++a) {
+        lo[a] = std::max(host_cell_of(w->lo[a], o[a], g.inv_h), 0);
+        hi[a] = std::min(host_cell_of(w->hi[a], o[a], g.inv_h), dim[a] - 1);
+    }
+    g.windowed = 1;
+    g.wlx = lo[0];
+    g.whx = hi[0];
+    g.wly = lo[1];
+    g.why = hi[1];
+    g.wlz = lo[2];
+    g.whz = hi[2];
+    // boundary cells whose points can fall outside the box: only where the
+    // bound lies inside the target's bounding box [origin, bbox_max]
+    int tl[3], th[3];
+    for (int a = 0; a < 3; ++a) {
+        tl[a] = w->lo[a] > o[a] ? lo[a] : -1;
+        th[a] = w->hi[a] < t->bbox_max[a] ? hi[a] : -1;
+    }
+    g.tlx = tl[0];
+    g.thx = th[0];
+    g.tly = tl[1];
+    g.thy = th[1];
+    g.tlz = tl[2];
+    g.thz = th[2];
+    g.wlox = w->lo[0];
+    g.wloy = w->lo[1];
+    g.wloz = w->lo[2];
+    g.whix = w->hi[0];
+    g.whiy = w->hi[1];
+    g.whiz = w->hi[2];
+    return PC_OK;
 }
 
 size_t pc_gicp_work_bytes(void) { return pc_gicp_work_size(); }

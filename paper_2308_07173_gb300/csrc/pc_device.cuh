@@ -21,6 +21,7 @@ constexpr unsigned long long EMPTY_KEY = ~0ull;
 constexpr int ST_NONFINITE = 1;
 constexpr int ST_SEARCH_LIMIT = 2;
 constexpr int ST_BAD_INDEX = 4;
+constexpr int ST_SHORT = 8;  // fewer than k target points in the window
 
 // Read-only view of a built target, passed by value to every search kernel.
 struct Grid {
@@ -47,7 +48,23 @@ struct Grid {
     const uint32_t* rank;
     int* status;
     unsigned long long* stats;  // [0] queries, [1] warp-search fallbacks, [2] exhaustive scans
+    // Search window (pc_set_window): only target points p with
+    // wlo <= p <= whi (componentwise) are searched.  [wl, wh] is the range of
+    // cells that can hold them (the whole grid when windowed == 0); a point
+    // in a cell strictly inside that range is inside the box (the cell rule
+    // is monotone), so only the range's boundary cells can hold points
+    // outside it -- and only where the bound lies inside the target's
+    // bounding box.  tl/th are those cells (-1 where no point can be cut).
+    int windowed;
+    int wlx, whx, wly, why, wlz, whz;
+    int tlx, thx, tly, thy, tlz, thz;
+    float wlox, wloy, wloz, whix, whiy, whiz;
 };
+
+__device__ __forceinline__ bool in_window(const Grid& g, float4 p) {
+    return p.x >= g.wlox && p.x <= g.whix && p.y >= g.wloy && p.y <= g.whiy && p.z >= g.wloz &&
+           p.z <= g.whiz;
+}
 
 __device__ __forceinline__ int cell_of(float v, float o, float inv_h) {
     float t = __fmul_rn(__fsub_rn(v, o), inv_h);

@@ -1,6 +1,7 @@
 // Host-side definitions shared by the library's translation units.
 #pragma once
 
+#include <cmath>
 #include <cstddef>
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -48,6 +49,7 @@ struct pc_target_s {
 struct pc_batch_s {
     uint32_t magic;
     pc_target_s* t;
+    pcdev::Grid g;  // the target's view when planned (window included)
     int n_scans;
     int k;
     float eps;
@@ -64,17 +66,35 @@ struct pc_batch_s {
     cudaStream_t captured_on;
 };
 
+// The whole grid as the search window (no point tests).
+inline void pc_clear_window(pcdev::Grid& g) {
+    g.windowed = 0;
+    g.wlx = 0;
+    g.whx = g.dimx - 1;
+    g.wly = 0;
+    g.why = g.dimy - 1;
+    g.wlz = 0;
+    g.whz = g.dimz - 1;
+    g.tlx = g.thx = g.tly = g.thy = g.tlz = g.thz = -1;
+    g.wlox = g.wloy = g.wloz = -INFINITY;
+    g.whix = g.whiy = g.whiz = INFINITY;
+}
+
 // grid_build.cu
 pc_status pc_build_grid(const float* xyz, int64_t M, const pc_build_opts& o, cudaStream_t s,
                         pc_target_s* t);
 void pc_free_grid(pc_target_s* t);
+
+// knn_window.cu: the window variant of the search kernels
+void* pc_knn_kernel_win(int mode, bool with_cov, bool batch);
+cudaError_t pc_knn_win_attrs();
 
 // knn_cov.cu
 cudaError_t pc_launch_knn(const pc_target_s* t, const float* q, int64_t N, int k, float eps,
                           int32_t* idx, float* d2, float* cov, float rho0, cudaStream_t s);
 cudaError_t pc_launch_cov(const pc_target_s* t, const int32_t* idx, int64_t N, int k, float eps,
                           float* cov, cudaStream_t s);
-cudaError_t pc_launch_knn_batch(const pc_target_s* t, const ScanDesc* scans_dev, int nscans,
+cudaError_t pc_launch_knn_batch(const pc_target_s* t, const pcdev::Grid& g, const ScanDesc* scans_dev, int nscans,
                                 int64_t total_tiles, int tile, int warps, int blocks, int k,
                                 float eps, bool with_cov, float rho0,
                                 unsigned long long* counter, cudaStream_t s);

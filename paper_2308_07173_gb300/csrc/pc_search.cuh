@@ -8,6 +8,16 @@
 
 namespace pcdev {
 
+// A point outside the window is handed to the visitor with x = +inf, so its
+// d2 is +inf and every threshold rejects it (a select, not a branch: the
+// visit loops keep their shape).  `test` is false off the window's
+// boundary cells; WIN = false compiles to nothing.
+template <bool WIN>
+__device__ __forceinline__ float4 window_cut(const Grid& g, bool test, float4 p) {
+    if (WIN && test && !in_window(g, p)) p.x = INFINITY;
+    return p;
+}
+
 // Distance from q to the nearer face of the cell slab [lo, hi] on one axis.
 __device__ __forceinline__ float slab_gap(float q, float o, int lo, int hi, float h) {
     const float flo = o + (float)lo * h;
@@ -43,11 +53,12 @@ __device__ __forceinline__ float certified_tau(const Grid& g, float qx, float qy
 // cell can hold a point within sqrt(tmax) of q, as f(position, point).
 // Rows along x are pruned by a conservative lower bound (the eta margin of
 // certified_tau); each surviving cell is a hash lookup.
-template <typename F>
+template <bool WIN = true, typename F>
 __device__ __forceinline__ void for_box_points(const Grid& g, float qx, float qy, float qz, int lx,
                                                int hx, int ly, int hy, int lz, int hz, float eta,
                                                float tmax, F&& f) {
     for (int cz = lz; cz <= hz; ++cz) {
+        const bool wz = WIN && g.windowed && (cz == g.tlz || cz == g.thz);
         const float zl = g.oz + (float)cz * g.h, zh = g.oz + (float)(cz + 1) * g.h;
         const float gz = fmaxf(fmaxf(zl - qz, qz - zh), 0.0f) - eta;
         const float gz2 = gz > 0.0f ? gz * gz : 0.0f;
@@ -56,13 +67,15 @@ __device__ __forceinline__ void for_box_points(const Grid& g, float qx, float qy
             const float gy = fmaxf(fmaxf(yl - qy, qy - yh), 0.0f) - eta;
             const float gyz2 = gz2 + (gy > 0.0f ? gy * gy : 0.0f);
             if (gyz2 * (1.0f - 0x1p-20f) > tmax) continue;
+            const bool wyz = wz || (WIN && g.windowed && (cy == g.tly || cy == g.thy));
             for (int cx = lx; cx <= hx; ++cx) {
                 const float xl = g.ox + (float)cx * g.h, xh = g.ox + (float)(cx + 1) * g.h;
                 const float gx = fmaxf(fmaxf(xl - qx, qx - xh), 0.0f) - eta;
                 const float lb2 = gyz2 + (gx > 0.0f ? gx * gx : 0.0f);
                 if (lb2 * (1.0f - 0x1p-20f) > tmax) continue;
+                const bool test = wyz || (WIN && g.windowed && (cx == g.tlx || cx == g.thx));
                 const uint2 r = lookup_cell(g, pack_key(cx, cy, cz, g.bx, g.by));
-                for (uint32_t i = 0; i < r.y; ++i) f(r.x + i, __ldg(&g.pts[r.x + i]));
+                for (uint32_t i = 0; i < r.y; ++i) f(r.x + i, window_cut<WIN>(g, test, __ldg(&g.pts[r.x + i])));
             }
         }
     }
@@ -91,11 +104,13 @@ __device__ __forceinline__ uint2 row_part(const Grid& g, float qx, float qy, flo
 // Same visit as for_box_points through the row index: every row of the box
 // is one contiguous range of pts.  Rows are resolved two at a time so their
 // index loads overlap.
-template <typename F>
+template <bool WIN = true, typename F>
 __device__ __forceinline__ void for_rows(const Grid& g, float qx, float qy, float qz, int lx, int hx,
                                          int ly, int hy, int lz, int hz, float eta, float tmax,
                                          F&& f) {
     const float tx = tmax * (1.0f + 0x1p-18f);
+    // the window's boundary cells along x are in every row of the box
+    const bool wx = WIN && g.windowed && (lx == g.tlx || hx == g.thx);
     int cy = ly, cz = lz;
     while (cz <= hz) {
         const int cy2 = cy < hy ? cy + 1 : ly;
@@ -103,8 +118,12 @@ __device__ __forceinline__ void for_rows(const Grid& g, float qx, float qy, floa
         const uint2 ra = row_part(g, qx, qy, qz, cy, cz, lx, hx, eta, tmax, tx);
         const uint2 rb = cz2 <= hz ? row_part(g, qx, qy, qz, cy2, cz2, lx, hx, eta, tmax, tx)
                                    : make_uint2(0u, 0u);
-        for (uint32_t i = 0; i < ra.y; ++i) f(ra.x + i, __ldg(&g.pts[ra.x + i]));
-        for (uint32_t i = 0; i < rb.y; ++i) f(rb.x + i, __ldg(&g.pts[rb.x + i]));
+        // a row on a boundary cell of the window tests its points (never in
+        // the whole-map variant, WIN = false)
+        const bool ta = WIN && (wx || cy == g.tly || cy == g.thy || cz == g.tlz || cz == g.thz);
+        const bool tb = WIN && (wx || cy2 == g.tly || cy2 == g.thy || cz2 == g.tlz || cz2 == g.thz);
+        for (uint32_t i = 0; i < ra.y; ++i) f(ra.x + i, window_cut<WIN>(g, ta, __ldg(&g.pts[ra.x + i])));
+        for (uint32_t i = 0; i < rb.y; ++i) f(rb.x + i, window_cut<WIN>(g, tb, __ldg(&g.pts[rb.x + i])));
         cy = cy2 < hy ? cy2 + 1 : ly;
         cz = cy2 < hy ? cz2 : cz2 + 1;
     }

@@ -66,6 +66,10 @@ class pc_build_opts(ctypes.Structure):
     ]
 
 
+class pc_window(ctypes.Structure):
+    _fields_ = [("lo", ctypes.c_float * 3), ("hi", ctypes.c_float * 3)]
+
+
 class pc_tune(ctypes.Structure):
     _fields_ = [("tile", ctypes.c_int), ("warps", ctypes.c_int), ("rho_scale", ctypes.c_float),
                 ("order", ctypes.c_int)]
@@ -120,6 +124,7 @@ SIGNATURES = {
     "pc_batch_run_noalloc": (_INT, [_VP, ctypes.POINTER(pc_scan), _INT, _INT, _F, _VP]),
     "pc_batch_scratch_bytes": (ctypes.c_size_t, [_INT]),
     "pc_batch_run_scratch": (_INT, [_VP, ctypes.POINTER(pc_scan), _INT, _INT, _F, _VP, ctypes.c_size_t, _VP]),
+    "pc_set_window": (_INT, [_VP, ctypes.POINTER(pc_window)]),
     "pc_gicp_work_bytes": (ctypes.c_size_t, []),
     "pc_gicp_linearize": (_INT, [_VP, _VP, _VP, _I64, _VP, _VP, _F, _VP, _VP, _VP, ctypes.c_size_t, _VP]),
     "pc_gicp_update": (_INT, [_VP, _F, _VP, _VP, _VP]),
@@ -234,6 +239,13 @@ def pc_batch_run_scratch(t, scans: Sequence[pc_scan], k: int, eps: float, scratc
                          scratch_bytes: int, stream) -> int:
     arr = (pc_scan * len(scans))(*scans)
     return load().pc_batch_run_scratch(t, arr, len(scans), k, eps, scratch_dev, scratch_bytes, stream)
+
+
+def pc_set_window(t, lo=None, hi=None) -> int:
+    if lo is None:
+        return load().pc_set_window(t, None)
+    w = pc_window((ctypes.c_float * 3)(*[float(v) for v in lo]), (ctypes.c_float * 3)(*[float(v) for v in hi]))
+    return load().pc_set_window(t, ctypes.byref(w))
 
 
 def pc_gicp_work_bytes() -> int:
@@ -385,6 +397,11 @@ class Target:
         rc = pc_knn_cov_host(self.handle, qp, n, k, float(eps), ptrs[0], ptrs[1], ptrs[2], _stream_handle(stream))
         _check(rc, "pc_knn_cov_host")
         return out
+
+    def set_window(self, lo=None, hi=None):
+        """Restrict later searches to the map points in the box [lo, hi]
+        (sliding-window submap); no arguments restore the whole map."""
+        _check(pc_set_window(self.handle, lo, hi), "pc_set_window")
 
     def gicp_work(self):
         """A device workspace for gicp_linearize (kept on the handle; calls

@@ -280,3 +280,27 @@ def test_degenerate_single_point_neighbourhood():
     g = np.repeat(np.array([[1.5, -2.0, 3.0]], np.float32), 6, 0)
     np.testing.assert_array_equal(_cov_of_all(g, -1), np.zeros((3, 3)))
     np.testing.assert_allclose(_cov_of_all(g, 0.5), np.diag([1, 1, 0.5]), atol=0)
+
+
+# ---------------------------------------------------------------- windowed search
+def test_window_knn_pins():
+    rng = np.random.default_rng(41)
+    p = rng.integers(0, 6, (60, 3)).astype(np.float32)  # lattice: exact d2, ties
+    q = rng.integers(0, 6, (15, 3)).astype(np.float32) + 0.5
+    inf = np.float32(np.inf)
+    # an infinite window is the whole map
+    i0, d0 = oracle.knn_brute(q, p, 7)
+    i1, d1 = oracle.knn_window(q, p, 7, [-inf] * 3, [inf] * 3)
+    np.testing.assert_array_equal(i0, i1)
+    np.testing.assert_array_equal(d0, d1)
+    # a half-space window: pure-Python brute force over the kept points
+    lo, hi = [-inf, 2.0, -inf], [inf, inf, 3.0]
+    iw, dw = oracle.knn_window(q, p, 7, lo, hi)
+    for n in range(len(q)):
+        keys = sorted((float(((q[n] - p[j]).astype(np.float64) ** 2).sum()), j) for j in range(len(p))
+                      if 2.0 <= p[j, 1] and p[j, 2] <= 3.0)
+        assert [j for _, j in keys[:7]] == list(iw[n])
+        assert all(p[j, 1] >= 2.0 and p[j, 2] <= 3.0 for j in iw[n])
+    # fewer than k points in the window
+    i2, d2 = oracle.knn_window(q, p, 7, [0, 0, 0], [0.5, 0.5, 0.5])
+    assert (i2 == -1).all() and np.isinf(d2).all()
