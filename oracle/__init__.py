@@ -14,6 +14,8 @@ Functions follow the plain definitions:
   for eps >= 0 the plane regularisation C' = I - (1-eps) n n^T with n the
   smallest-eigenvalue eigenvector (cyclic Jacobi).
 * ``eig_sym3(c6)``         -- the Jacobi eigen-solver on its own.
+* ``cov_weighted``         -- the covariance with kernel-descriptor weights
+  (Table I) on the neighbours.
 * ``gicp_transform`` / ``gicp_linearize`` -- one Gauss-Newton linearisation
   of GICP (Eq. 18-20) in binary64 on top of the nearest-point search.
 * ``window_mask`` / ``knn_window`` -- the search restricted to a box of the
@@ -70,6 +72,8 @@ def _load():
         lib.oracle_eig_sym3.restype = None
         lib.oracle_gicp_linearize.argtypes = [vp, vp, vp, i64, vp, vp, ctypes.c_float, vp, vp, i32]
         lib.oracle_gicp_linearize.restype = i32
+        lib.oracle_cov_weighted.argtypes = [vp, i64, vp, vp, i64, i32, f64, i32, vp, vp, vp]
+        lib.oracle_cov_weighted.restype = i32
         lib.oracle_gicp_transform.argtypes = [vp, vp, i64, vp]
         lib.oracle_gicp_transform.restype = None
         lib.oracle_default_threads.argtypes = []
@@ -240,6 +244,31 @@ def cov(p, idx, eps: float, threads: int = 0) -> np.ndarray:
     rc = _load().oracle_cov(_ptr(p), p.shape[0], _ptr(idx), n, k, float(eps), _ptr(out), int(threads))
     if rc != 0:
         raise ValueError(f"oracle_cov: bad arguments (rc={rc})")
+    return out
+
+
+KERNELS = {"none": 0, "rbf": 1, "gaussian": 2, "polynomial": 3, "hi": 4, "laplacian": 5}
+
+
+def cov_weighted(p, q, idx, eps: float, kernel: str, sigma: float = 1.0, alpha: float = 1.0, c: float = 0.0,
+                 d: float = 1.0, origin=(0.0, 0.0, 0.0)) -> np.ndarray:
+    """Kernel-descriptor weighted covariance (Sec. III-C1, Table I): weights
+    w_j = K(q, p_j) on the neighbours of each row, weighted mean and moments,
+    then the plane regularisation for eps >= 0; binary64 [n,6].  Polynomial
+    and HI take coordinates relative to `origin` (the target's bounding-box
+    minimum).  Rows with a non-positive total weight are NaN."""
+    p, q = _f32x3(p), _f32x3(q)
+    idx = np.ascontiguousarray(idx, dtype=np.int32)
+    n, k = idx.shape
+    if q.shape[0] != n:
+        raise ValueError("q and idx rows differ")
+    prm = np.array([sigma, alpha, c, d], np.float64)
+    o = np.ascontiguousarray(origin, dtype=np.float64).reshape(3)
+    out = np.empty((n, 6), np.float64)
+    rc = _load().oracle_cov_weighted(_ptr(p), p.shape[0], _ptr(q), _ptr(idx), n, k, float(eps), KERNELS[kernel],
+                                     _ptr(prm), _ptr(o), _ptr(out))
+    if rc != 0:
+        raise ValueError(f"oracle_cov_weighted: bad arguments (rc={rc})")
     return out
 
 

@@ -602,3 +602,111 @@ int oracle_gicp_linearize(void *vt, const float *map_cov, const float *src, int6
     free(nd);
     return 0;
 }
+
+/* ------------------------------------------------------------------ */
+/* Kernel-descriptor weighted covariance (Sec. III-C1, Table I).       */
+/* ------------------------------------------------------------------ */
+/* The paper computes the per-point covariance "using the kernel
+ * descriptors" of Table I without stating where the kernel enters; this
+ * reads it as a weight on every neighbour, w_j = K(q, p_j), in a weighted
+ * mean and weighted second moments:
+ *     W = sum w_j,  mu = sum w_j p_j / W,
+ *     C = sum w_j (p_j - mu)(p_j - mu)^T / W,
+ * then the same plane regularisation as oracle_cov_one (eps >= 0).  The
+ * kernels, with x = q and y = p_j:
+ *     1 RBF         exp(-|x - y|^2 sigma)
+ *     2 Gaussian    exp(-|x - y|^2 / (2 sigma^2))
+ *     3 Polynomial  (alpha <x', y'> + c)^d
+ *     4 HI          sum_i min(x'_i, y'_i) / sum_i x'_i
+ *     5 Laplacian   exp(-|x - y| / sigma)
+ * where x' = x - o, y' = y - o are coordinates relative to o, the target's
+ * bounding-box minimum (Polynomial and HI depend on absolute coordinates;
+ * this fixes their origin to the map's own).  Everything is binary64 from
+ * the binary32 inputs.  A row whose total weight is not positive and finite
+ * is NaN. */
+static double kd_weight(int type, const double *x, const double *y, const double *o, double sigma,
+                        double alpha, double c, double d)
+{
+    double r2 = 0, dot = 0, mn = 0, sx = 0;
+    for (int a = 0; a < 3; a++) {
+        const double e = x[a] - y[a];
+        r2 += e * e;
+        const double xa = x[a] - o[a], ya = y[a] - o[a];
+        dot += xa * ya;
+        mn += xa < ya ? xa : ya;
+        sx += xa;
+    }
+    switch (type) {
+    case 1: return exp(-r2 * sigma);
+    case 2: return exp(-r2 / (2.0 * sigma * sigma));
+    case 3: return pow(alpha * dot + c, d);
+    case 4: return mn / sx;
+    case 5: return exp(-sqrt(r2) / sigma);
+    }
+    return 1.0;
+}
+
+void oracle_cov_weighted_one(const float *p, const int32_t *nb, int k, const float *q, int type,
+                             const double *prm, const double *o, double eps, double *out)
+{
+    double x[3] = {q[0], q[1], q[2]};
+    double W = 0, mu[3] = {0, 0, 0};
+    double *w = (double *)malloc(sizeof(double) * k);
+    for (int j = 0; j < k; j++) {
+        const double y[3] = {p[3 * (int64_t)nb[j]], p[3 * (int64_t)nb[j] + 1], p[3 * (int64_t)nb[j] + 2]};
+        w[j] = kd_weight(type, x, y, o, prm[0], prm[1], prm[2], prm[3]);
+        W += w[j];
+        for (int a = 0; a < 3; a++) mu[a] += w[j] * y[a];
+    }
+    if (!(W > 0) || !isfinite(W)) {
+        for (int e = 0; e < 6; e++) out[e] = NAN;
+        free(w);
+        return;
+    }
+    for (int a = 0; a < 3; a++) mu[a] /= W;
+    double C[6] = {0, 0, 0, 0, 0, 0};
+    for (int j = 0; j < k; j++) {
+        double d[3];
+        for (int a = 0; a < 3; a++) d[a] = (double)p[3 * (int64_t)nb[j] + a] - mu[a];
+        C[0] += w[j] * d[0] * d[0];
+        C[1] += w[j] * d[0] * d[1];
+        C[2] += w[j] * d[0] * d[2];
+        C[3] += w[j] * d[1] * d[1];
+        C[4] += w[j] * d[1] * d[2];
+        C[5] += w[j] * d[2] * d[2];
+    }
+    free(w);
+    for (int e = 0; e < 6; e++) C[e] /= W;
+    if (eps < 0) {
+        memcpy(out, C, sizeof(C));
+        return;
+    }
+    double n[3] = {0, 0, 1};
+    if (C[0] + C[3] + C[5] > 1e-20) {
+        double ev[3], V[9];
+        oracle_eig_sym3(C, ev, V);
+        for (int r = 0; r < 3; r++) n[r] = V[3 * r + 0];
+        double nn = sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+        for (int r = 0; r < 3; r++) n[r] /= nn;
+    }
+    double f = 1.0 - eps;
+    out[0] = 1.0 - f * n[0] * n[0];
+    out[1] = -f * n[0] * n[1];
+    out[2] = -f * n[0] * n[2];
+    out[3] = 1.0 - f * n[1] * n[1];
+    out[4] = -f * n[1] * n[2];
+    out[5] = 1.0 - f * n[2] * n[2];
+}
+
+/* q: [n,3], idx: [n,k] rows into p: [m,3]; prm = (sigma, alpha, c, d);
+ * o = the target's bounding-box minimum.  Returns -1 / -2 as oracle_cov. */
+int oracle_cov_weighted(const float *p, int64_t m, const float *q, const int32_t *idx, int64_t n, int k,
+                        double eps, int type, const double *prm, const double *o, double *cov)
+{
+    if (k < 1 || n < 0 || type < 0 || type > 5) return -1;
+    for (int64_t i = 0; i < n * (int64_t)k; i++)
+        if (idx[i] < 0 || (int64_t)idx[i] >= m) return -2;
+    for (int64_t i = 0; i < n; i++)
+        oracle_cov_weighted_one(p, idx + i * k, k, q + 3 * i, type, prm, o, eps, cov + 6 * i);
+    return 0;
+}
