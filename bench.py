@@ -216,7 +216,7 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--ref-sample", type=int, default=16384)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4", "c5", "gicp", "window"],
+    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4", "c5", "gicp", "window", "kernel"],
                     help="c2 is the headline; the others print their own line")
     ap.add_argument("--duration", type=float, default=3.0, help="c4: seconds of arrivals")
     args = ap.parse_args()
@@ -226,7 +226,7 @@ def main():
         return run_reference(args)
     if args.workload != "c2":
         return {"c1": run_c1, "c3": run_c3, "c4": run_c4, "c5": run_c5, "gicp": run_gicp,
-                "window": run_window}[args.workload](args)
+                "window": run_window, "kernel": run_kernel}[args.workload](args)
     return run_c2(args)
 
 
@@ -589,6 +589,49 @@ def run_window(args):
                     "kernel": "k_knn<0,true,true> (window variant)"},
           whole_map_ms=ms_full, latency_ms={"p50": all_ms[len(all_ms) // 2], "max": all_ms[-1]}, clocks=clk,
           gpu_launches=reps)
+    t.close()
+    return 0
+
+
+def run_kernel(args):
+    """The C2 workload with the covariance weighted by the Laplacian kernel
+    descriptor (Table I; the paper's best), sigma = 0.1 m: the search, then
+    the weighted covariance pass; timed next to the plain fused search."""
+    import torch
+
+    from paper_2308_07173_gb300 import pc
+    from paper_2308_07173_gb300 import workloads as W
+
+    pc.load()
+    q, m = W.scan_vs_map(MAP_POINTS)
+    N = len(q)
+    md, qd = torch.from_numpy(m).cuda(), torch.from_numpy(q).cuda()
+    t = pc.Target(md)
+    idx = torch.empty((N, K_NN), dtype=torch.int32, device="cuda")
+    d2 = torch.empty((N, K_NN), dtype=torch.float32, device="cuda")
+    cov = torch.empty((N, 6), dtype=torch.float32, device="cuda")
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    s = torch.cuda.Stream()
+    reps = max(5, min(args.steps, 200))
+    ms_plain, _ = _timed(lambda: t.knn_cov(qd, K_NN, EPS, idx, d2, cov, stream=s), flush, reps, s)
+    t.set_cov_kernel("laplacian", sigma=0.1)
+    clocks = Clocks(torch.cuda.current_device())
+    clocks.start()
+    ms, all_ms = _timed(lambda: t.knn_cov(qd, K_NN, EPS, idx, d2, cov, stream=s), flush, reps, s)
+    clk = clocks.stop()
+    st = t.sync_status(s)
+    assert st == pc.PC_OK, pc.pc_status_string(st)
+    alg = N * (12 + 8 * K_NN + 24)
+    peak, kind = peaks()
+    ach = alg / (ms / 1e3) / 1e9
+    _line("query points/sec for kNN(k=20) + Laplacian-weighted cov, 131k scan vs 2M map", N / (ms / 1e3), UNIT, ms,
+          args, {"workload": "kernel_laplacian_c2_scan131k_map2M_k20", "n_queries": N, "map_points": MAP_POINTS,
+                 "sigma": 0.1, "l2": "flushed by a 256 MB write before every timed call"},
+          roofline={"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                    "traffic": None, "peak_source": kind, "algorithmic_bytes_queries_only": alg,
+                    "kernel": "k_knn<0,false,false> + k_cov_weighted"},
+          plain_fused_ms=ms_plain, latency_ms={"p50": all_ms[len(all_ms) // 2], "max": all_ms[-1]}, clocks=clk,
+          gpu_launches=2 * reps)
     t.close()
     return 0
 

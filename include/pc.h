@@ -184,6 +184,41 @@ typedef struct {
  * on an axis; the handle errors of pc_knn. */
 PC_API pc_status pc_set_window(pc_target t, const pc_window *w);
 
+/* Kernel descriptors of Table I (Sec. III-C1: the covariance is computed
+ * "using the kernel descriptors"). */
+typedef enum {
+    PC_KERNEL_NONE = 0,       /* plain covariance */
+    PC_KERNEL_RBF = 1,        /* exp(-|x - y|^2 sigma) */
+    PC_KERNEL_GAUSSIAN = 2,   /* exp(-|x - y|^2 / (2 sigma^2)) */
+    PC_KERNEL_POLYNOMIAL = 3, /* (alpha <x', y'> + c)^d */
+    PC_KERNEL_HI = 4,         /* sum_i min(x'_i, y'_i) / sum_i x'_i */
+    PC_KERNEL_LAPLACIAN = 5   /* exp(-|x - y| / sigma) */
+} pc_kernel_type;
+
+typedef struct {
+    int type; /* pc_kernel_type */
+    float sigma, alpha, c, d;
+} pc_cov_kernel;
+
+/* Weights the covariance of every later fused search on this target --
+ * pc_knn_cov, pc_knn_cov_host and the batched forms -- by a kernel
+ * descriptor: for query x = q and its neighbours y = p_j, w_j = K(x, y_j),
+ * W = sum w_j, mu = sum w_j p_j / W, C = sum w_j (p_j - mu)(p_j - mu)^T / W,
+ * then the plane regularisation for eps >= 0 as before.  Polynomial and HI
+ * use coordinates relative to the target's bounding-box minimum (x' = x - o,
+ * y' = y - o).  The paper names the kernels but not how they enter the
+ * covariance; this weighted form is the reading.  Per query the weights and
+ * moments are binary32 (two passes shifted by the nearest neighbour).  A row
+ * whose total weight is not positive and finite (a polynomial can make it
+ * so) is NaN.  The neighbours are unchanged: the search runs as without a
+ * kernel and a second launch forms the weighted covariances.  NULL or type
+ * PC_KERNEL_NONE restores the plain covariance.  pc_cov is not affected (it
+ * has no query points).  A batch plan keeps the kernel set when it was
+ * planned.  Host-only.  Errors: PC_ERR_INVALID_ARG for an unknown type, a
+ * non-finite parameter, sigma < 0 (RBF) or sigma <= 0 (Gaussian,
+ * Laplacian); the handle errors of pc_knn. */
+PC_API pc_status pc_set_cov_kernel(pc_target t, const pc_cov_kernel *kd);
+
 /* pc_knn and pc_cov fused in one launch; identical results to the two calls. */
 PC_API pc_status pc_knn_cov(pc_target t, const float *q_dev, int64_t N, int k, float eps,
                      int32_t *idx_dev, float *d2_dev, float *cov_dev, pc_stream s);

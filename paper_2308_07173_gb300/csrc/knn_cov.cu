@@ -78,7 +78,10 @@ cudaError_t pc_launch_knn(const pc_target_s* t, const float* q, int64_t N, int k
     const int tile = clamp_tile(t->tune.tile);
     const int warps = clamp_warps(t->tune.warps);
     TileArgs a{k, eps, t->tune.rho_scale > 0 ? t->tune.rho_scale : 0.9f, t->tune.order == 0 ? 1 : 0};
-    const bool with_cov = cov != nullptr;
+    // kernel-descriptor weights: search without the covariance, then a
+    // weighted covariance pass over the neighbours
+    const bool weighted = cov != nullptr && t->ck.type != 0;
+    const bool with_cov = cov != nullptr && !weighted;
     const int mode = search_mode(k);
     const size_t smem = (size_t)warps * warp_smem_bytes(mode);
     const int64_t tiles = (N + tile - 1) / tile;
@@ -86,9 +89,11 @@ cudaError_t pc_launch_knn(const pc_target_s* t, const float* q, int64_t N, int k
     Grid g = t->g;
     float* covp = with_cov ? cov : nullptr;
     void* args[] = {&g, (void*)&q, (void*)&N, (void*)&tile, &a, &rho0, &idx, &d2, &covp};
-    return with_kernel<false>(mode, with_cov, g.windowed != 0, [&](void* kern) {
+    e = with_kernel<false>(mode, with_cov, g.windowed != 0, [&](void* kern) {
         return cudaLaunchKernel(kern, dim3((unsigned)blocks), dim3(warps * 32), args, smem, s);
     });
+    if (e == cudaSuccess && weighted) e = pc_launch_cov_weighted(g, t->ck, q, idx, N, k, eps, cov, s);
+    return e;
 }
 
 cudaError_t pc_launch_cov(const pc_target_s* t, const int32_t* idx, int64_t N, int k, float eps,
@@ -100,18 +105,24 @@ cudaError_t pc_launch_cov(const pc_target_s* t, const int32_t* idx, int64_t N, i
     return cudaGetLastError();
 }
 
-cudaError_t pc_launch_knn_batch(const pc_target_s* t, const Grid& gv, const ScanDesc* scans_dev, int nscans,
+cudaError_t pc_launch_knn_batch(const pc_target_s* t, const Grid& gv, const CovKernel& ck,
+                                const ScanDesc* scans_dev, int nscans, int64_t max_n,
                                 int64_t total_tiles, int tile, int warps, int blocks, int k,
                                 float eps, bool with_cov, float rho0,
                                 unsigned long long* counter, cudaStream_t s) {
     TileArgs a{k, eps, t->tune.rho_scale > 0 ? t->tune.rho_scale : 0.9f, 0};
     const int mode = search_mode(k);
     const size_t smem = (size_t)warps * warp_smem_bytes(mode);
+    const bool weighted = with_cov && ck.type != 0;
+    const bool fused_cov = with_cov && !weighted;
     Grid g = gv;
     void* args[] = {&g, (void*)&scans_dev, &nscans, &total_tiles, &tile, &a, &rho0, &counter};
-    return with_kernel<true>(mode, with_cov, g.windowed != 0, [&](void* kern) {
+    cudaError_t e = with_kernel<true>(mode, fused_cov, g.windowed != 0, [&](void* kern) {
         return cudaLaunchKernel(kern, dim3((unsigned)blocks), dim3(warps * 32), args, smem, s);
     });
+    if (e == cudaSuccess && weighted)
+        e = pc_launch_cov_weighted_batch(g, ck, scans_dev, nscans, max_n, k, eps, s);
+    return e;
 }
 
 int pc_knn_batch_blocks(int k, bool with_cov, int warps) {

@@ -76,7 +76,7 @@ extern "C" pc_status pc_batch_run_noalloc(pc_target t, const pc_scan* scans, int
     const int tile = t->tune.tile < 1 ? 32 : (t->tune.tile > 32 ? 32 : t->tune.tile);
     const int warps = t->tune.warps < 1 ? 4 : (t->tune.warps > 8 ? 8 : t->tune.warps);
     ScanDesc table[PC_NOALLOC_MAX_SCANS];
-    int64_t tiles = 0;
+    int64_t tiles = 0, max_n = 0;
     for (int i = 0; i < n_scans; ++i) {
         table[i].q = scans[i].q_dev;
         table[i].n = scans[i].n;
@@ -85,6 +85,7 @@ extern "C" pc_status pc_batch_run_noalloc(pc_target t, const pc_scan* scans, int
         table[i].cov = scans[i].cov_dev;
         table[i].tile0 = tiles;
         tiles += (scans[i].n + tile - 1) / tile;
+        if (scans[i].n > max_n) max_n = scans[i].n;
     }
     if (tiles == 0) return PC_OK;
 
@@ -99,7 +100,7 @@ extern "C" pc_status pc_batch_run_noalloc(pc_target t, const pc_scan* scans, int
                                     cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), st);
     if (e == cudaSuccess)
-        e = pc_launch_knn_batch(t, t->g, table_dev, n_scans, tiles, tile, warps, blocks, k, eps, any_cov,
+        e = pc_launch_knn_batch(t, t->g, t->ck, table_dev, n_scans, max_n, tiles, tile, warps, blocks, k, eps, any_cov,
                                 pc_rho0(t, k), counter, st);
     return pc_from_cuda(e);
 }

@@ -384,6 +384,7 @@ pc_status pc_batch_plan(pc_target t, const pc_scan* scans, int n_scans, int k, f
     b->magic = PC_MAGIC_LIVE;
     b->t = t;
     b->g = t->g;
+    b->ck = t->ck;
     b->n_scans = n_scans;
     b->k = k;
     b->eps = eps;
@@ -401,6 +402,7 @@ pc_status pc_batch_plan(pc_target t, const pc_scan* scans, int n_scans, int k, f
         hs[i].tile0 = tiles;
         tiles += (scans[i].n + b->tile - 1) / b->tile;
         queries += scans[i].n;
+        b->max_n = std::max<int64_t>(b->max_n, scans[i].n);
     }
     b->total_tiles = tiles;
     b->total_queries = queries;
@@ -431,7 +433,7 @@ pc_status pc_batch_run(pc_batch b, pc_stream s) {
     if (st == nullptr) {  // the legacy stream cannot be captured: launch directly
         cudaError_t e = cudaMemsetAsync(b->counter, 0, sizeof(unsigned long long), st);
         if (e == cudaSuccess)
-            e = pc_launch_knn_batch(b->t, b->g, b->scans_dev, b->n_scans, b->total_tiles, b->tile,
+            e = pc_launch_knn_batch(b->t, b->g, b->ck, b->scans_dev, b->n_scans, b->max_n, b->total_tiles, b->tile,
                                     b->warps, b->blocks, b->k, b->eps, b->with_cov, rho0,
                                     b->counter, st);
         return pc_from_cuda(e);
@@ -444,7 +446,7 @@ pc_status pc_batch_run(pc_batch b, pc_stream s) {
         cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
         if (e != cudaSuccess) return pc_from_cuda(e);
         cudaError_t e1 = cudaMemsetAsync(b->counter, 0, sizeof(unsigned long long), st);
-        cudaError_t e2 = pc_launch_knn_batch(b->t, b->g, b->scans_dev, b->n_scans, b->total_tiles,
+        cudaError_t e2 = pc_launch_knn_batch(b->t, b->g, b->ck, b->scans_dev, b->n_scans, b->max_n, b->total_tiles,
                                              b->tile, b->warps, b->blocks, b->k, b->eps,
                                              b->with_cov, rho0, b->counter, st);
         e = cudaStreamEndCapture(st, &b->graph);
@@ -494,7 +496,7 @@ pc_status pc_batch_run_scratch(pc_target t, const pc_scan* scans, int n_scans, i
     const int tile = std::min(std::max(t->tune.tile, 1), 32);
     const int warps = std::min(std::max(t->tune.warps, 1), 8);
     std::vector<ScanDesc> hs(n_scans);
-    int64_t tiles = 0;
+    int64_t tiles = 0, max_n = 0;
     for (int i = 0; i < n_scans; ++i) {
         hs[i].q = scans[i].q_dev;
         hs[i].n = scans[i].n;
@@ -503,6 +505,7 @@ pc_status pc_batch_run_scratch(pc_target t, const pc_scan* scans, int n_scans, i
         hs[i].cov = scans[i].cov_dev;
         hs[i].tile0 = tiles;
         tiles += (scans[i].n + tile - 1) / tile;
+        max_n = std::max<int64_t>(max_n, scans[i].n);
     }
     if (tiles == 0) return PC_OK;
     cudaStream_t st = (cudaStream_t)s;
@@ -514,7 +517,7 @@ pc_status pc_batch_run_scratch(pc_target t, const pc_scan* scans, int n_scans, i
                                     cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), st);
     if (e == cudaSuccess)
-        e = pc_launch_knn_batch(t, t->g, table, n_scans, tiles, tile, warps, blocks, k, eps, any_cov,
+        e = pc_launch_knn_batch(t, t->g, t->ck, table, n_scans, max_n, tiles, tile, warps, blocks, k, eps, any_cov,
                                 pc_rho0(t, k), counter, st);
     return pc_from_cuda(e);
 }
@@ -583,6 +586,44 @@ pc_status pc_set_window(pc_target t, const pc_window* w) {
     g.whix = w->hi[0];
     g.whiy = w->hi[1];
     g.whiz = w->hi[2];
+    return PC_OK;
+}
+
+pc_status pc_set_cov_kernel(pc_target t, const pc_cov_kernel* kd) {
+    pc_status r = check_target(t);
+    if (r != PC_OK) return r;
+    CovKernel ck{};
+    if (kd && kd->type != PC_KERNEL_NONE) {
+        if (kd->type < PC_KERNEL_RBF || kd->type > PC_KERNEL_LAPLACIAN) return PC_ERR_INVALID_ARG;
+        if (!std::isfinite(kd->sigma) || !std::isfinite(kd->alpha) || !std::isfinite(kd->c) ||
+            !std::isfinite(kd->d))
+            return PC_ERR_INVALID_ARG;
+        const double sg = kd->sigma;
+        ck.type = kd->type;
+        switch (kd->type) {
+            case PC_KERNEL_RBF:
+                if (!(sg >= 0)) return PC_ERR_INVALID_ARG;
+                ck.s = (float)sg;
+                break;
+            case PC_KERNEL_GAUSSIAN:
+                if (!(sg > 0)) return PC_ERR_INVALID_ARG;
+                ck.s = (float)(1.0 / (2.0 * sg * sg));
+                break;
+            case PC_KERNEL_LAPLACIAN:
+                if (!(sg > 0)) return PC_ERR_INVALID_ARG;
+                ck.s = (float)(1.0 / sg);
+                break;
+            default:
+                break;
+        }
+        ck.alpha = kd->alpha;
+        ck.c = kd->c;
+        ck.d = kd->d;
+        ck.ox = t->g.ox;
+        ck.oy = t->g.oy;
+        ck.oz = t->g.oz;
+    }
+    t->ck = ck;
     return PC_OK;
 }
 

@@ -12,6 +12,15 @@
 constexpr uint32_t PC_MAGIC_LIVE = 0x70637467u;  // "pctg"
 constexpr uint32_t PC_MAGIC_DEAD = 0xdeadbeefu;
 
+// Kernel-descriptor weights of the covariance (pc_set_cov_kernel), as the
+// device sees them: s = sigma (RBF), 1 / (2 sigma^2) (Gaussian) or
+// 1 / sigma (Laplacian); o = the target's bounding-box minimum.
+struct CovKernel {
+    int type;
+    float s, alpha, c, d;
+    float ox, oy, oz;
+};
+
 // One scan of a batched launch, as the persistent kernel sees it.
 struct ScanDesc {
     const float* q;
@@ -44,12 +53,15 @@ struct pc_target_s {
     // staging for pc_knn_cov_host, grown on demand
     void* stage;
     size_t stage_bytes;
+    CovKernel ck;  // covariance weights (type 0: none)
 };
 
 struct pc_batch_s {
     uint32_t magic;
     pc_target_s* t;
     pcdev::Grid g;  // the target's view when planned (window included)
+    CovKernel ck;   // and its covariance weights
+    int64_t max_n;  // largest scan
     int n_scans;
     int k;
     float eps;
@@ -94,7 +106,8 @@ cudaError_t pc_launch_knn(const pc_target_s* t, const float* q, int64_t N, int k
                           int32_t* idx, float* d2, float* cov, float rho0, cudaStream_t s);
 cudaError_t pc_launch_cov(const pc_target_s* t, const int32_t* idx, int64_t N, int k, float eps,
                           float* cov, cudaStream_t s);
-cudaError_t pc_launch_knn_batch(const pc_target_s* t, const pcdev::Grid& g, const ScanDesc* scans_dev, int nscans,
+cudaError_t pc_launch_knn_batch(const pc_target_s* t, const pcdev::Grid& g, const CovKernel& ck,
+                                const ScanDesc* scans_dev, int nscans, int64_t max_n,
                                 int64_t total_tiles, int tile, int warps, int blocks, int k,
                                 float eps, bool with_cov, float rho0,
                                 unsigned long long* counter, cudaStream_t s);
@@ -108,6 +121,14 @@ cudaError_t pc_launch_gicp_linearize(const pc_target_s* t, const float* map_cov,
                                      float r0, cudaStream_t s);
 cudaError_t pc_launch_gicp_update(const double* lin, float lambda, float* pose, double* xi,
                                   cudaStream_t s);
+
+// cov_weighted.cu
+cudaError_t pc_launch_cov_weighted(const pcdev::Grid& g, const CovKernel& ck, const float* q,
+                                   const int32_t* idx, int64_t N, int k, float eps, float* cov,
+                                   cudaStream_t s);
+cudaError_t pc_launch_cov_weighted_batch(const pcdev::Grid& g, const CovKernel& ck,
+                                         const ScanDesc* scans_dev, int nscans, int64_t max_n, int k,
+                                         float eps, cudaStream_t s);
 
 // pc_api.cu
 float pc_rho0(const pc_target_s* t, int k);

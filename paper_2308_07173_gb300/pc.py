@@ -66,6 +66,14 @@ class pc_build_opts(ctypes.Structure):
     ]
 
 
+class pc_cov_kernel(ctypes.Structure):
+    _fields_ = [("type", ctypes.c_int), ("sigma", ctypes.c_float), ("alpha", ctypes.c_float),
+                ("c", ctypes.c_float), ("d", ctypes.c_float)]
+
+
+PC_KERNELS = {"none": 0, "rbf": 1, "gaussian": 2, "polynomial": 3, "hi": 4, "laplacian": 5}
+
+
 class pc_window(ctypes.Structure):
     _fields_ = [("lo", ctypes.c_float * 3), ("hi", ctypes.c_float * 3)]
 
@@ -125,6 +133,7 @@ SIGNATURES = {
     "pc_batch_scratch_bytes": (ctypes.c_size_t, [_INT]),
     "pc_batch_run_scratch": (_INT, [_VP, ctypes.POINTER(pc_scan), _INT, _INT, _F, _VP, ctypes.c_size_t, _VP]),
     "pc_set_window": (_INT, [_VP, ctypes.POINTER(pc_window)]),
+    "pc_set_cov_kernel": (_INT, [_VP, ctypes.POINTER(pc_cov_kernel)]),
     "pc_gicp_work_bytes": (ctypes.c_size_t, []),
     "pc_gicp_linearize": (_INT, [_VP, _VP, _VP, _I64, _VP, _VP, _F, _VP, _VP, _VP, ctypes.c_size_t, _VP]),
     "pc_gicp_update": (_INT, [_VP, _F, _VP, _VP, _VP]),
@@ -246,6 +255,14 @@ def pc_set_window(t, lo=None, hi=None) -> int:
         return load().pc_set_window(t, None)
     w = pc_window((ctypes.c_float * 3)(*[float(v) for v in lo]), (ctypes.c_float * 3)(*[float(v) for v in hi]))
     return load().pc_set_window(t, ctypes.byref(w))
+
+
+def pc_set_cov_kernel(t, kernel: str = "none", sigma: float = 1.0, alpha: float = 1.0, c: float = 0.0,
+                      d: float = 1.0) -> int:
+    if kernel == "none":
+        return load().pc_set_cov_kernel(t, None)
+    kd = pc_cov_kernel(PC_KERNELS[kernel], sigma, alpha, c, d)
+    return load().pc_set_cov_kernel(t, ctypes.byref(kd))
 
 
 def pc_gicp_work_bytes() -> int:
@@ -397,6 +414,13 @@ class Target:
         rc = pc_knn_cov_host(self.handle, qp, n, k, float(eps), ptrs[0], ptrs[1], ptrs[2], _stream_handle(stream))
         _check(rc, "pc_knn_cov_host")
         return out
+
+    def set_cov_kernel(self, kernel: str = "none", sigma: float = 1.0, alpha: float = 1.0, c: float = 0.0,
+                       d: float = 1.0):
+        """Weight the covariances of later fused searches by a kernel
+        descriptor of Table I ('rbf', 'gaussian', 'polynomial', 'hi',
+        'laplacian'); 'none' restores the plain covariance."""
+        _check(pc_set_cov_kernel(self.handle, kernel, sigma, alpha, c, d), "pc_set_cov_kernel")
 
     def set_window(self, lo=None, hi=None):
         """Restrict later searches to the map points in the box [lo, hi]
