@@ -351,7 +351,7 @@ def run_c2(args):
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic, "peak_source": peak_kind,
                          "algorithmic_bytes": alg_bytes, "U_p": U_p, "U_c": U_c,
-                         "kernel": "k_knn<1,true> (fused search + covariance)"},
+                         "kernel": "k_knn<0,1,0> (fused search + covariance, whole-map variant)"},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 12 * N,
                     "d2h_bytes_per_step": N * (8 * K_NN + 24)},
             "clocks": clk,
