@@ -20,6 +20,8 @@ Functions follow the plain definitions:
   of GICP (Eq. 18-20) in binary64 on top of the nearest-point search.
 * ``window_mask`` / ``knn_window`` -- the search restricted to a box of the
   map (sliding-window submap, Sec. III-C3).
+* ``wall_detect``          -- voxel filter, 2-D vote ground filter, Euclidean
+  clustering and the wall's quadratic fit (Sec. III-D).
 * ``gicp_update`` / ``so3_exp`` -- the step that follows it: solve
   (H + lam I) xi = -b, move the pose by Exp(omega) on the left.
 
@@ -74,6 +76,9 @@ def _load():
         lib.oracle_gicp_linearize.restype = i32
         lib.oracle_cov_weighted.argtypes = [vp, i64, vp, vp, i64, i32, f64, i32, vp, vp, vp]
         lib.oracle_cov_weighted.restype = i32
+        lib.oracle_wall_detect.argtypes = [vp, i64, ctypes.c_float, ctypes.c_float, i32, ctypes.c_float, i32,
+                                           ctypes.c_float, ctypes.c_float, vp, vp, vp, vp, vp, vp]
+        lib.oracle_wall_detect.restype = i64
         lib.oracle_gicp_transform.argtypes = [vp, vp, i64, vp]
         lib.oracle_gicp_transform.restype = None
         lib.oracle_default_threads.argtypes = []
@@ -204,6 +209,27 @@ def knn_window(q, p, k: int, lo, hi, threads: int = 0):
         i, d = t.knn(q, k, threads)
         t.close()
     return sel[i].astype(np.int32), d
+
+
+def wall_detect(pts, voxel: float = 0.2, cell2d: float = 0.5, min_votes: int = 3, tol: float = 0.5,
+                min_cluster: int = 10, max_range: float = 128.0, max_height: float = 16.0) -> dict:
+    """Ground filter by 2-D voting, Euclidean clustering of the vertical
+    voxels and the wall's quadratic fit (Sec. III-D, Eq. 24-30): see
+    oracle_wall_detect in oracle.c for the exact definition."""
+    pts = _f32x3(pts)
+    n = pts.shape[0]
+    cent = np.empty((max(n, 1), 3), np.float32)
+    vert = np.empty(max(n, 1), np.int32)
+    lab = np.empty(max(n, 1), np.int64)
+    wl = np.zeros(1, np.int64)
+    wc = np.zeros(1, np.int64)
+    beta = np.empty(3, np.float64)
+    nv = _load().oracle_wall_detect(_ptr(pts), n, voxel, cell2d, int(min_votes), tol, int(min_cluster), max_range,
+                                    max_height, _ptr(cent), _ptr(vert), _ptr(lab), _ptr(wl), _ptr(beta), _ptr(wc))
+    if nv < 0:
+        raise ValueError("oracle_wall_detect: bad arguments")
+    return {"centroids": cent[:nv].copy(), "vertical": vert[:nv].astype(bool), "labels": lab[:nv].copy(),
+            "wall_label": int(wl[0]), "wall_count": int(wc[0]), "beta": beta.copy(), "d_w": float(beta[0])}
 
 
 def so3_exp(w) -> np.ndarray:

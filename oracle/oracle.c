@@ -710,3 +710,223 @@ int oracle_cov_weighted(const float *p, int64_t m, const float *q, const int32_t
         oracle_cov_weighted_one(p, idx + i * k, k, q + 3 * i, type, prm, o, eps, cov + 6 * i);
     return 0;
 }
+
+/* ------------------------------------------------------------------ */
+/* Ground filter by 2-D voting and wall clustering (Sec. III-D, Eq.    */
+/* 24-30).                                                             */
+/* ------------------------------------------------------------------ */
+/* Points are in the vehicle body frame (x forward, y left).  Steps, in the
+ * paper's order:
+ *  1. voxel filter: voxel (i,j,k) = floor(fl(p * fl(1/v))) per axis; points
+ *     whose voxel lies outside |i|,|j| < 2^(bxy-1), |k| < 2^(bz-1) (the
+ *     configured range) or that are not finite are dropped.  Voxels are
+ *     numbered in ascending key order, key = (i+o) | (j+o) << bxy |
+ *     (k+oz) << 2 bxy; each voxelised point is the centroid of its points,
+ *     summed in binary64 in input order, divided by the count and rounded to
+ *     binary32 (Eq. 24: one representative per voxel);
+ *  2. vote: each voxel votes for the 2-D cell floor(fl(c_x * fl(1/g))),
+ *     floor(fl(c_y * fl(1/g))) of its centroid; a voxel is a vertical
+ *     feature when its cell holds more than min_votes voxels, ground
+ *     otherwise (Eq. 25 and the hyper-parameter comparison);
+ *  3. Euclidean clustering of the vertical voxels: two are linked when the
+ *     pinned binary32 d2 of their centroids is <= fl(tol * tol); clusters
+ *     are the connected components, labelled by their smallest voxel index
+ *     (Eq. 26, read as the usual single-linkage tree clustering the text
+ *     names);
+ *  4. the wall: among clusters of at least min_cluster voxels on the right
+ *     (fl(min y + max y) < 0), the longest, length = fl(max x - min x);
+ *     ties to the smaller label (Eq. 27, H = the cluster's length);
+ *  5. y = b0 + b1 x + b2 x^2 by least squares over the wall's centroids,
+ *     normal equations in binary64 (Eq. 28); d_w = b0 is y at the vehicle
+ *     origin x = 0 (Eq. 29); b1, b2 are the path coefficients (Eq. 30).
+ * Outputs per voxel (in key order): centroid, vertical flag, label (-1 for
+ * ground).  Returns the number of voxels, or a negative code. */
+typedef struct {
+    uint64_t key;
+    int64_t idx;
+} keyidx;
+
+static int keyidx_cmp(const void *a, const void *b)
+{
+    const keyidx *x = (const keyidx *)a, *y = (const keyidx *)b;
+    if (x->key != y->key) return x->key < y->key ? -1 : 1;
+    return x->idx < y->idx ? -1 : (x->idx > y->idx);
+}
+
+static int64_t uf_find(int64_t *par, int64_t a)
+{
+    while (par[a] != a) a = par[a];
+    return a;
+}
+
+static int bits_to_hold(int64_t n)
+{
+    int b = 1;
+    while (((int64_t)1 << b) < n) b++;
+    return b;
+}
+
+int64_t oracle_wall_detect(const float *pts, int64_t n, float voxel, float cell2d, int min_votes, float tol,
+                           int min_cluster, float max_range, float max_height, float *cent, int32_t *vertical,
+                           int64_t *label, int64_t *wall_label, double *beta, int64_t *wall_count)
+{
+    if (n < 0 || !(voxel > 0) || !(cell2d > 0) || !(tol > 0) || !(max_range > 0) || !(max_height > 0)) return -1;
+    const float inv_v = 1.0f / voxel, inv_g = 1.0f / cell2d;
+    const int64_t rxy = (int64_t)ceil(max_range / voxel) + 1, rz = (int64_t)ceil(max_height / voxel) + 1;
+    const int bxy = bits_to_hold(2 * rxy), bz = bits_to_hold(2 * rz);
+    if (2 * bxy + bz > 63) return -1;
+    const int64_t oxy = (int64_t)1 << (bxy - 1), oz = (int64_t)1 << (bz - 1);
+    keyidx *ki = (keyidx *)malloc(sizeof(keyidx) * (n > 0 ? n : 1));
+    int64_t m = 0;
+    for (int64_t i = 0; i < n; i++) {
+        const float *p = pts + 3 * i;
+        if (!isfinite(p[0]) || !isfinite(p[1]) || !isfinite(p[2])) continue;
+        const double fi = floor((double)(p[0] * inv_v)), fj = floor((double)(p[1] * inv_v)),
+                     fk = floor((double)(p[2] * inv_v));
+        if (fabs(fi) >= (double)oxy || fabs(fj) >= (double)oxy || fabs(fk) >= (double)oz) continue;
+        const uint64_t ci = (uint64_t)((int64_t)fi + oxy), cj = (uint64_t)((int64_t)fj + oxy),
+                       ck = (uint64_t)((int64_t)fk + oz);
+        ki[m].key = ci | (cj << bxy) | (ck << (2 * bxy));
+        ki[m].idx = i;
+        m++;
+    }
+    qsort(ki, (size_t)m, sizeof(keyidx), keyidx_cmp);
+    /* 1. voxel centroids */
+    int64_t nv = 0;
+    for (int64_t s = 0; s < m;) {
+        int64_t e = s;
+        double sx = 0, sy = 0, sz = 0;
+        while (e < m && ki[e].key == ki[s].key) {
+            const float *p = pts + 3 * ki[e].idx;
+            sx += p[0];
+            sy += p[1];
+            sz += p[2];
+            e++;
+        }
+        const double c = (double)(e - s);
+        cent[3 * nv] = (float)(sx / c);
+        cent[3 * nv + 1] = (float)(sy / c);
+        cent[3 * nv + 2] = (float)(sz / c);
+        nv++;
+        s = e;
+    }
+    free(ki);
+    /* 2. votes per 2-D cell (sorted cell keys) */
+    keyidx *ck = (keyidx *)malloc(sizeof(keyidx) * (nv > 0 ? nv : 1));
+    for (int64_t v = 0; v < nv; v++) {
+        const int64_t u = (int64_t)floor((double)(cent[3 * v] * inv_g));
+        const int64_t w = (int64_t)floor((double)(cent[3 * v + 1] * inv_g));
+        ck[v].key = ((uint64_t)(u + ((int64_t)1 << 31)) << 32) | (uint64_t)(w + ((int64_t)1 << 31));
+        ck[v].idx = v;
+    }
+    qsort(ck, (size_t)nv, sizeof(keyidx), keyidx_cmp);
+    for (int64_t s = 0; s < nv;) {
+        int64_t e = s;
+        while (e < nv && ck[e].key == ck[s].key) e++;
+        for (int64_t t = s; t < e; t++) vertical[ck[t].idx] = (e - s) > min_votes;
+        s = e;
+    }
+    free(ck);
+    /* 3. clustering of the vertical voxels: brute force pairs, union-find
+     * hooking the larger root under the smaller */
+    int64_t *par = (int64_t *)malloc(sizeof(int64_t) * (nv > 0 ? nv : 1));
+    for (int64_t v = 0; v < nv; v++) par[v] = v;
+    const float tol2 = tol * tol;
+    for (int64_t a = 0; a < nv; a++) {
+        if (!vertical[a]) continue;
+        for (int64_t b = a + 1; b < nv; b++) {
+            if (!vertical[b]) continue;
+            if (sqdist(cent + 3 * a, cent + 3 * b) <= tol2) {
+                int64_t ra = uf_find(par, a), rb = uf_find(par, b);
+                if (ra != rb) {
+                    if (ra < rb) par[rb] = ra;
+                    else par[ra] = rb;
+                }
+            }
+        }
+    }
+    for (int64_t v = 0; v < nv; v++) label[v] = vertical[v] ? uf_find(par, v) : -1;
+    free(par);
+    /* 4. the wall */
+    float *mnx = (float *)malloc(sizeof(float) * (nv > 0 ? nv : 1));
+    float *mxx = (float *)malloc(sizeof(float) * (nv > 0 ? nv : 1));
+    float *mny = (float *)malloc(sizeof(float) * (nv > 0 ? nv : 1));
+    float *mxy = (float *)malloc(sizeof(float) * (nv > 0 ? nv : 1));
+    int64_t *cnt = (int64_t *)calloc((size_t)(nv > 0 ? nv : 1), sizeof(int64_t));
+    for (int64_t v = 0; v < nv; v++) {
+        if (label[v] < 0) continue;
+        const int64_t L = label[v];
+        const float x = cent[3 * v], y = cent[3 * v + 1];
+        if (cnt[L] == 0) {
+            mnx[L] = mxx[L] = x;
+            mny[L] = mxy[L] = y;
+        } else {
+            if (x < mnx[L]) mnx[L] = x;
+            if (x > mxx[L]) mxx[L] = x;
+            if (y < mny[L]) mny[L] = y;
+            if (y > mxy[L]) mxy[L] = y;
+        }
+        cnt[L]++;
+    }
+    int64_t best = -1;
+    float best_len = -1.0f;
+    for (int64_t L = 0; L < nv; L++) {
+        if (cnt[L] < min_cluster || cnt[L] == 0) continue;
+        if (!(mny[L] + mxy[L] < 0.0f)) continue;
+        const float len = mxx[L] - mnx[L];
+        if (len > best_len) {
+            best_len = len;
+            best = L;
+        }
+    }
+    *wall_label = best;
+    *wall_count = best >= 0 ? cnt[best] : 0;
+    /* 5. least squares y = b0 + b1 x + b2 x^2 */
+    beta[0] = beta[1] = beta[2] = NAN;
+    if (best >= 0) {
+        double A[3][3] = {{0}}, r[3] = {0};
+        for (int64_t v = 0; v < nv; v++) {
+            if (label[v] != best) continue;
+            const double x = cent[3 * v], y = cent[3 * v + 1];
+            const double f[3] = {1.0, x, x * x};
+            for (int a = 0; a < 3; a++) {
+                for (int b = 0; b < 3; b++) A[a][b] += f[a] * f[b];
+                r[a] += f[a] * y;
+            }
+        }
+        /* Gaussian elimination with partial pivoting */
+        double M[3][4];
+        for (int a = 0; a < 3; a++) {
+            for (int b = 0; b < 3; b++) M[a][b] = A[a][b];
+            M[a][3] = r[a];
+        }
+        int ok = 1;
+        for (int c = 0; c < 3 && ok; c++) {
+            int piv = c;
+            for (int a = c + 1; a < 3; a++)
+                if (fabs(M[a][c]) > fabs(M[piv][c])) piv = a;
+            if (!(fabs(M[piv][c]) > 0)) {
+                ok = 0;
+                break;
+            }
+            for (int b = 0; b < 4; b++) {
+                double t = M[c][b];
+                M[c][b] = M[piv][b];
+                M[piv][b] = t;
+            }
+            for (int a = 0; a < 3; a++) {
+                if (a == c) continue;
+                const double f = M[a][c] / M[c][c];
+                for (int b = c; b < 4; b++) M[a][b] -= f * M[c][b];
+            }
+        }
+        if (ok)
+            for (int a = 0; a < 3; a++) beta[a] = M[a][3] / M[a][a];
+    }
+    free(mnx);
+    free(mxx);
+    free(mny);
+    free(mxy);
+    free(cnt);
+    return nv;
+}
