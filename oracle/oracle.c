@@ -718,8 +718,9 @@ int oracle_cov_weighted(const float *p, int64_t m, const float *q, const int32_t
 /* Points are in the vehicle body frame (x forward, y left).  Steps, in the
  * paper's order:
  *  1. voxel filter: voxel (i,j,k) = floor(fl(p * fl(1/v))) per axis; points
- *     whose voxel lies outside |i|,|j| < 2^(bxy-1), |k| < 2^(bz-1) (the
- *     configured range) or that are not finite are dropped.  Voxels are
+ *     whose voxel lies outside -2^(b-1) <= i <= 2^(b-1) - 2 (b = bxy for i, j
+ *     and bz for k, sized to hold the configured range) or that are not
+ *     finite are dropped.  Voxels are
  *     numbered in ascending key order, key = (i+o) | (j+o) << bxy |
  *     (k+oz) << 2 bxy; each voxelised point is the centroid of its points,
  *     summed in binary64 in input order, divided by the count and rounded to
@@ -783,7 +784,11 @@ int64_t oracle_wall_detect(const float *pts, int64_t n, float voxel, float cell2
         if (!isfinite(p[0]) || !isfinite(p[1]) || !isfinite(p[2])) continue;
         const double fi = floor((double)(p[0] * inv_v)), fj = floor((double)(p[1] * inv_v)),
                      fk = floor((double)(p[2] * inv_v));
-        if (fabs(fi) >= (double)oxy || fabs(fj) >= (double)oxy || fabs(fk) >= (double)oz) continue;
+        /* kept: -o <= i <= o - 2, so a field never reaches all ones (that key
+         * marks a dropped point) */
+        if (fi < -(double)oxy || fi > (double)(oxy - 2) || fj < -(double)oxy || fj > (double)(oxy - 2) ||
+            fk < -(double)oz || fk > (double)(oz - 2))
+            continue;
         const uint64_t ci = (uint64_t)((int64_t)fi + oxy), cj = (uint64_t)((int64_t)fj + oxy),
                        ck = (uint64_t)((int64_t)fk + oz);
         ki[m].key = ci | (cj << bxy) | (ck << (2 * bxy));
