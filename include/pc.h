@@ -363,6 +363,75 @@ PC_API pc_status pc_gicp_linearize(pc_target map, const float *map_cov_dev, cons
 PC_API pc_status pc_gicp_update(const double *lin_dev, float lambda, float *pose_dev,
                                 double *xi_dev, pc_stream s);
 
+/* ---- Wall detection (Sec. III-D, Eq. 24-30) ---- */
+
+typedef struct pc_wall_s *pc_wall; /* opaque, library-owned */
+
+typedef struct {
+    float voxel;      /* voxel edge of the voxel filter, m (default 0.2) */
+    float cell2d;     /* edge of the 2-D voting cells, m (default 0.2) */
+    int min_votes;    /* a 2-D cell holding more voxels than this is a vertical
+                         feature; the rest is ground (default 2) */
+    float tol;        /* Euclidean clustering distance, m (default 0.45) */
+    int min_cluster;  /* smallest cluster (voxels) that can be the wall (10) */
+    float max_range;  /* |x|, |y| kept, m (default 128) */
+    float max_height; /* |z| kept, m (default 16) */
+} pc_wall_opts;
+
+typedef struct {
+    int64_t n_voxels;   /* voxels after the voxel filter */
+    int64_t n_vertical; /* of those, vertical features */
+    int64_t wall_label; /* the wall cluster's label (its smallest voxel index), -1: none */
+    int64_t wall_count; /* voxels in the wall cluster */
+    float wall_length;  /* its extent along x, m */
+    double beta[3];     /* y = beta0 + beta1 x + beta2 x^2 over the wall (Eq. 28); NaN if none */
+    double d_w;         /* beta0: the wall's lateral offset at the vehicle origin (Eq. 29) */
+} pc_wall_result;
+
+PC_API void pc_wall_default_opts(pc_wall_opts *o);
+
+/* A detector for scans of up to max_points points (vehicle body frame: x
+ * forward, y left, z up).  Allocates every device buffer once (about
+ * 150 B per point); pc_wall_detect allocates nothing.  Errors:
+ * PC_ERR_INVALID_ARG (max_points < 1 or >= 2^31, non-positive or non-finite
+ * sizes, a key range over 63 bits), PC_ERR_OOM. */
+PC_API pc_status pc_wall_create(int64_t max_points, const pc_wall_opts *o, pc_wall *out);
+
+/* One scan, asynchronous on `s` (pts_dev: f32 [n,3] device memory, n <=
+ * max_points):
+ *  1. voxel filter: voxel (i,j,k) = floor(fl(p * fl(1/voxel))); points that
+ *     are not finite or whose voxel lies outside the configured range are
+ *     dropped; voxels are numbered in ascending key order; each voxelised
+ *     point is the centroid of its points (binary64 sum in input order,
+ *     rounded to binary32);
+ *  2. 2-D voting: each voxel votes for the cell floor(fl(c * fl(1/cell2d)))
+ *     of its centroid's x, y (a hash table, Eq. 25); voxels in cells with more
+ *     than min_votes votes are vertical features, the rest ground;
+ *  3. Euclidean clustering of the vertical voxels: linked when the pinned
+ *     binary32 squared distance of their centroids is <= fl(tol^2);
+ *     clusters are connected components labelled by their smallest voxel
+ *     index (Eq. 26);
+ *  4. the wall: the longest cluster (fl(max x - min x)) of >= min_cluster
+ *     voxels on the right (fl(min y + max y) < 0), ties to the smaller
+ *     label (Eq. 27);
+ *  5. y = b0 + b1 x + b2 x^2 by least squares over the wall's centroids in
+ *     binary64 (Eq. 28), d_w = b0 (Eq. 29); b1, b2 shape the wall-following
+ *     path of Eq. 30.
+ * Voxels, flags and labels are deterministic; the fit repeats bit for bit.
+ * Errors: PC_ERR_INVALID_ARG (bad handle, n < 0 or > max_points, NULL
+ * points), PC_ERR_BAD_POINTER (host points). */
+PC_API pc_status pc_wall_detect(pc_wall w, const float *pts_dev, int64_t n, pc_stream s);
+
+/* Synchronises `s` and reads the last detection: the summary, and (each
+ * optional) per voxel the centroid (f32 [n_voxels,3]), vertical flag (i32)
+ * and cluster label (i32, -1 for ground) into host arrays of at least
+ * n_voxels rows.  Returns PC_ERR_SEARCH_LIMIT if an internal iteration cap
+ * was reached (a hash table or a union-find chase; not expected). */
+PC_API pc_status pc_wall_get(pc_wall w, pc_stream s, pc_wall_result *res, float *centroids_host,
+                             int32_t *vertical_host, int32_t *labels_host);
+
+PC_API void pc_wall_destroy(pc_wall w);
+
 PC_API const char *pc_status_string(pc_status st);
 
 /* Library version string, e.g. "pc 0.1 sm_103a". */

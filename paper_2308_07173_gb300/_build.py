@@ -21,7 +21,7 @@ BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libpc.so")
 
 SOURCES = ["pc_api.cu", "grid_build.cu", "knn_cov.cu", "knn_window.cu", "noalloc.cu", "gicp.cu",
-           "cov_weighted.cu"]
+           "cov_weighted.cu", "wall.cu"]
 HEADERS = ["pc_device.cuh", "pc_internal.h", "pc_search.cuh", "knn_kernels.cuh"]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

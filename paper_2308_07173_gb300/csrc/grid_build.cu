@@ -433,6 +433,51 @@ cudaError_t radix_sort(u64*& keys, uint32_t*& vals, u64* keys_alt, uint32_t* val
     return cudaGetLastError();
 }
 
+}  // namespace
+
+// Sort and scan on caller buffers (used by the wall detector, which sizes
+// everything once at creation).
+size_t pc_sort_temp_words(int64_t n) {
+    const int64_t nb = (n + RS_TILE - 1) / RS_TILE;
+    return (size_t)256 * (size_t)std::max<int64_t>(nb, 1) + 256;
+}
+
+cudaError_t pc_radix_sort_pairs(u64** keys, uint32_t** vals, u64* keys_alt, uint32_t* vals_alt,
+                                int64_t n, int nbits, uint32_t* temp, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    const int nb = (int)((n + RS_TILE - 1) / RS_TILE);
+    uint32_t* counts = temp;
+    uint32_t* totals = temp + (size_t)256 * nb;
+    u64* k = *keys;
+    uint32_t* v = *vals;
+    for (int shift = 0; shift < nbits; shift += 8) {
+        k_rs_hist<<<nb, RS_NT, 0, s>>>(k, n, shift, counts, nb);
+        k_rs_scan_digits<<<256, SC_NT, 0, s>>>(counts, nb, totals);
+        k_rs_scatter<<<nb, RS_NT, 0, s>>>(k, v, keys_alt, vals_alt, n, shift, counts, nb, totals);
+        std::swap(k, keys_alt);
+        std::swap(v, vals_alt);
+    }
+    *keys = k;
+    *vals = v;
+    return cudaGetLastError();
+}
+
+size_t pc_scan_temp_words(int64_t n) {
+    return (size_t)std::max<int64_t>((n + SC_TILE - 1) / SC_TILE, 1);
+}
+
+cudaError_t pc_scan_exclusive(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* total_dev,
+                              uint32_t* temp, cudaStream_t s) {
+    if (n <= 0) return cudaMemsetAsync(total_dev, 0, sizeof(uint32_t), s);
+    const int nb = (int)((n + SC_TILE - 1) / SC_TILE);
+    k_scan_reduce<<<nb, SC_NT, 0, s>>>(in, n, temp);
+    k_scan_top<<<1, SC_NT, 0, s>>>(temp, nb, total_dev);
+    k_scan_down<<<nb, SC_NT, 0, s>>>(in, out, n, temp);
+    return cudaGetLastError();
+}
+
+namespace {
+
 // occupied cells for trial h
 cudaError_t count_cells(const float* xyz, int64_t M, const float o[3], float h, u64* set,
                         int log2cap, unsigned long long* counter, cudaStream_t s,

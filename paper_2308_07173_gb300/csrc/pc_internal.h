@@ -96,6 +96,12 @@ inline void pc_clear_window(pcdev::Grid& g) {
 pc_status pc_build_grid(const float* xyz, int64_t M, const pc_build_opts& o, cudaStream_t s,
                         pc_target_s* t);
 void pc_free_grid(pc_target_s* t);
+size_t pc_sort_temp_words(int64_t n);
+cudaError_t pc_radix_sort_pairs(unsigned long long** keys, uint32_t** vals, unsigned long long* keys_alt,
+                                uint32_t* vals_alt, int64_t n, int nbits, uint32_t* temp, cudaStream_t s);
+size_t pc_scan_temp_words(int64_t n);
+cudaError_t pc_scan_exclusive(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* total_dev,
+                              uint32_t* temp, cudaStream_t s);
 
 // knn_window.cu: the window variant of the search kernels
 void* pc_knn_kernel_win(int mode, bool with_cov, bool batch);

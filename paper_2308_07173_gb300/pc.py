@@ -74,6 +74,18 @@ class pc_cov_kernel(ctypes.Structure):
 PC_KERNELS = {"none": 0, "rbf": 1, "gaussian": 2, "polynomial": 3, "hi": 4, "laplacian": 5}
 
 
+class pc_wall_opts(ctypes.Structure):
+    _fields_ = [("voxel", ctypes.c_float), ("cell2d", ctypes.c_float), ("min_votes", ctypes.c_int),
+                ("tol", ctypes.c_float), ("min_cluster", ctypes.c_int), ("max_range", ctypes.c_float),
+                ("max_height", ctypes.c_float)]
+
+
+class pc_wall_result(ctypes.Structure):
+    _fields_ = [("n_voxels", ctypes.c_int64), ("n_vertical", ctypes.c_int64), ("wall_label", ctypes.c_int64),
+                ("wall_count", ctypes.c_int64), ("wall_length", ctypes.c_float), ("beta", ctypes.c_double * 3),
+                ("d_w", ctypes.c_double)]
+
+
 class pc_window(ctypes.Structure):
     _fields_ = [("lo", ctypes.c_float * 3), ("hi", ctypes.c_float * 3)]
 
@@ -134,6 +146,11 @@ SIGNATURES = {
     "pc_batch_run_scratch": (_INT, [_VP, ctypes.POINTER(pc_scan), _INT, _INT, _F, _VP, ctypes.c_size_t, _VP]),
     "pc_set_window": (_INT, [_VP, ctypes.POINTER(pc_window)]),
     "pc_set_cov_kernel": (_INT, [_VP, ctypes.POINTER(pc_cov_kernel)]),
+    "pc_wall_default_opts": (None, [ctypes.POINTER(pc_wall_opts)]),
+    "pc_wall_create": (_INT, [_I64, ctypes.POINTER(pc_wall_opts), ctypes.POINTER(_VP)]),
+    "pc_wall_detect": (_INT, [_VP, _VP, _I64, _VP]),
+    "pc_wall_get": (_INT, [_VP, _VP, ctypes.POINTER(pc_wall_result), _VP, _VP, _VP]),
+    "pc_wall_destroy": (None, [_VP]),
     "pc_gicp_work_bytes": (ctypes.c_size_t, []),
     "pc_gicp_linearize": (_INT, [_VP, _VP, _VP, _I64, _VP, _VP, _F, _VP, _VP, _VP, ctypes.c_size_t, _VP]),
     "pc_gicp_update": (_INT, [_VP, _F, _VP, _VP, _VP]),
@@ -500,6 +517,57 @@ class Batch:
     def close(self):
         if self._h is not None:
             pc_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class WallDetector:
+    """Ground filter, wall clustering and wall fit for scans in the vehicle
+    body frame (pc_wall_*, Sec. III-D)."""
+
+    def __init__(self, max_points: int, **opts):
+        o = pc_wall_opts()
+        load().pc_wall_default_opts(ctypes.byref(o))
+        for k, v in opts.items():
+            if not hasattr(o, k):
+                raise TypeError(f"unknown option {k}")
+            setattr(o, k, v)
+        h = ctypes.c_void_p()
+        _check(load().pc_wall_create(int(max_points), ctypes.byref(o), ctypes.byref(h)), "pc_wall_create")
+        self._h = h.value
+        self.max_points = int(max_points)
+
+    def detect(self, pts, stream=None):
+        torch = _torch()
+        pts = _dev_tensor(pts, torch.float32, 3, "pts")
+        _check(load().pc_wall_detect(self._h, pts.data_ptr(), pts.shape[0], _stream_handle(stream)), "pc_wall_detect")
+
+    def result(self, arrays: bool = False, stream=None) -> dict:
+        r = pc_wall_result()
+        st = load().pc_wall_get(self._h, _stream_handle(stream), ctypes.byref(r), None, None, None)
+        if st not in (PC_OK, PC_ERR_SEARCH_LIMIT):
+            _check(st, "pc_wall_get")
+        out = {"n_voxels": r.n_voxels, "n_vertical": r.n_vertical, "wall_label": r.wall_label,
+               "wall_count": r.wall_count, "wall_length": r.wall_length, "beta": list(r.beta), "d_w": r.d_w,
+               "status": st}
+        if arrays and r.n_voxels > 0:
+            n = r.n_voxels
+            cent = np.empty((n, 3), np.float32)
+            vert = np.empty(n, np.int32)
+            lab = np.empty(n, np.int32)
+            st = load().pc_wall_get(self._h, _stream_handle(stream), ctypes.byref(r), cent.ctypes.data,
+                                    vert.ctypes.data, lab.ctypes.data)
+            out.update(centroids=cent, vertical=vert.astype(bool), labels=lab, status=st)
+        return out
+
+    def close(self):
+        if self._h:
+            load().pc_wall_destroy(self._h)
             self._h = None
 
     def __del__(self):

@@ -286,6 +286,21 @@ def oval_4000_pit() -> Track:
 
 
 # ---------------------------------------------------------------- workloads
+def body_frame_scan(track: Optional[Track] = None, s0: float = 130.0, w0: float = 1.0, heading_dev: float = 0.0,
+                    seed: int = 9) -> np.ndarray:
+    """A ray-cast scan expressed in the vehicle body frame of its pose (x
+    forward along the heading, y left, z up from the ground), float32."""
+    tr = track or oval_1500()
+    g = rng_for(seed)
+    pts = tr.raycast(s0, w0, heading_dev, g).astype(np.float64)
+    pos, tan, nrm = tr.pose(np.array([s0]))
+    o = pos[0] + nrm[0] * w0
+    yaw = math.atan2(tan[0, 1], tan[0, 0]) + heading_dev
+    c, s_ = math.cos(yaw), math.sin(yaw)
+    dx, dy = pts[:, 0] - o[0], pts[:, 1] - o[1]
+    return np.c_[c * dx + s_ * dy, -s_ * dx + c * dy, pts[:, 2]].astype(np.float32)
+
+
 def scan_vs_map(map_points: int = 2_000_000, map_seed: int = 2, scan_seed: int = 3,
                 track: Optional[Track] = None):
     """One 128 x 1024 ray-cast scan at a random pose and the map it is queried
