@@ -216,7 +216,7 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--ref-sample", type=int, default=16384)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4", "c5", "gicp", "window", "kernel", "wall"],
+    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4", "c5", "gicp", "window", "kernel", "wall", "append"],
                     help="c2 is the headline; the others print their own line")
     ap.add_argument("--duration", type=float, default=3.0, help="c4: seconds of arrivals")
     args = ap.parse_args()
@@ -226,7 +226,8 @@ def main():
         return run_reference(args)
     if args.workload != "c2":
         return {"c1": run_c1, "c3": run_c3, "c4": run_c4, "c5": run_c5, "gicp": run_gicp,
-                "window": run_window, "kernel": run_kernel, "wall": run_wall}[args.workload](args)
+                "window": run_window, "kernel": run_kernel, "wall": run_wall,
+                "append": run_append}[args.workload](args)
     return run_c2(args)
 
 
@@ -681,6 +682,62 @@ def run_wall(args):
                     "algorithmic_bytes_points_only": alg, "kernel": "pc_wall_detect (graph of ~40 launches)"},
           eager_ms=ms_eager, latency_ms={"p50": all_ms[len(all_ms) // 2], "max": all_ms[-1]}, clocks=clk,
           gpu_launches=reps)
+    return 0
+
+
+def run_append(args):
+    """Incremental map update: the 2M-point map built from 1.8M points with
+    200k appended (no main-grid rebuild), the C2 scan searched over the union
+    (main + delta searches and the exact merge), next to the same search on
+    a map built whole; also the append and compaction times."""
+    import torch
+
+    from paper_2308_07173_gb300 import pc
+    from paper_2308_07173_gb300 import workloads as W
+
+    pc.load()
+    q, m = W.scan_vs_map(MAP_POINTS)
+    N = len(q)
+    md, qd = torch.from_numpy(m).cuda(), torch.from_numpy(q).cuda()
+    n_main = MAP_POINTS - 200_000
+    whole = pc.Target(md)
+    t = pc.Target(md[:n_main].contiguous())
+    s = torch.cuda.Stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    t.append(md[n_main:].contiguous(), stream=s)
+    s.synchronize()
+    append_ms = (time.perf_counter() - t0) * 1e3
+    idx = torch.empty((N, K_NN), dtype=torch.int32, device="cuda")
+    d2 = torch.empty((N, K_NN), dtype=torch.float32, device="cuda")
+    cov = torch.empty((N, 6), dtype=torch.float32, device="cuda")
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    reps = max(5, min(args.steps, 200))
+    ms_whole, _ = _timed(lambda: whole.knn_cov(qd, K_NN, EPS, idx, d2, cov, stream=s), flush, reps, s)
+    ref = idx.clone()
+    clocks = Clocks(torch.cuda.current_device())
+    clocks.start()
+    ms, all_ms = _timed(lambda: t.knn_cov(qd, K_NN, EPS, idx, d2, cov, stream=s), flush, reps, s)
+    clk = clocks.stop()
+    assert t.sync_status(s) == pc.PC_OK
+    assert torch.equal(ref, idx)
+    t0 = time.perf_counter()
+    t.compact(stream=s)
+    s.synchronize()
+    compact_ms = (time.perf_counter() - t0) * 1e3
+    alg = N * (12 + 8 * K_NN + 24)
+    peak, kind = peaks()
+    _line("query points/sec for kNN(k=20)+cov over a 2M map grown by 200k appended points", N / (ms / 1e3), UNIT,
+          ms, args, {"workload": "append_c2_scan131k_map1.8M_plus200k_k20", "n_queries": N, "map_main": n_main,
+                     "appended": MAP_POINTS - n_main, "l2": "flushed by a 256 MB write before every timed call"},
+          roofline={"bound": "hbm", "achieved": alg / (ms / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
+                    "frac": alg / (ms / 1e3) / 1e9 / peak, "traffic": None, "peak_source": kind,
+                    "algorithmic_bytes_queries_only": alg, "kernel": "k_knn (main) + k_knn (delta) + k_merge"},
+          whole_map_ms=ms_whole, append_ms=append_ms, compact_ms=compact_ms,
+          latency_ms={"p50": all_ms[len(all_ms) // 2], "max": all_ms[-1]}, clocks=clk, gpu_launches=3 * reps)
+    t.close()
+    whole.close()
     return 0
 
 

@@ -101,6 +101,8 @@ typedef struct {
     int dims[3];        /* cells per axis */
     int64_t device_bytes; /* device memory held by the handle */
     float rho_hint[64]; /* calibrated first search radius for k = 1..64 (0 if k > M) */
+    int64_t delta_m;    /* points appended by pc_target_append and not yet compacted
+                           (m counts the main grid only) */
 } pc_target_info;
 
 /* Counters kept by the search kernels since the last reset (one atomic per
@@ -218,6 +220,30 @@ typedef struct {
  * non-finite parameter, sigma < 0 (RBF) or sigma <= 0 (Gaussian,
  * Laplacian); the handle errors of pc_knn. */
 PC_API pc_status pc_set_cov_kernel(pc_target t, const pc_cov_kernel *kd);
+
+/* Incremental map update (the map grows while it is used, Sec. III-C3's
+ * unified map): appends n points (device f32 [n,3]) to the target without
+ * rebuilding its grid.  They get the indices M + (their position among all
+ * appended points), and every later search -- pc_knn, pc_knn_cov,
+ * pc_knn_cov_host, pc_cov, pc_gicp_linearize -- answers over the whole
+ * union exactly: the main grid is searched as usual, then each query's row
+ * is completed from a small grid over the appended points, visiting only
+ * those strictly closer than the row's k-th neighbour (a certified box), so
+ * results equal a target built from all the points at once (idx and d2 bit
+ * for bit; the covariance to its rounding).  The delta grid is rebuilt from all appended points at
+ * each call (O(appended) work; the main grid is never touched).  Windows and
+ * covariance kernels apply to both.  The batched forms refuse a target with
+ * appended points (PC_ERR_INVALID_ARG): compact it first.  Synchronous with
+ * respect to `s` (it builds a grid); allocates.  Errors: PC_ERR_NONFINITE
+ * (nothing is appended), PC_ERR_INVALID_ARG (n < 0, M + appended >= 2^31),
+ * PC_ERR_BAD_POINTER, PC_ERR_OOM. */
+PC_API pc_status pc_target_append(pc_target t, const float *xyz_dev, int64_t n, pc_stream s);
+
+/* Folds the appended points into a new main grid over all M + appended
+ * points (same indices, same handle, window and settings kept) and drops the
+ * delta.  A no-op without appended points.  Batch plans made before it must
+ * be made again (pc_batch_run refuses them). */
+PC_API pc_status pc_target_compact(pc_target t, pc_stream s);
 
 /* pc_knn and pc_cov fused in one launch; identical results to the two calls. */
 PC_API pc_status pc_knn_cov(pc_target t, const float *q_dev, int64_t N, int k, float eps,

@@ -195,8 +195,8 @@ __device__ __forceinline__ bool pair_terms(const float* R, float px, float py, f
 }
 
 __global__ void __launch_bounds__(GICP_THREADS) k_gicp_linearize(
-    Grid g, const float* __restrict__ map_cov, const float* __restrict__ src, int64_t n,
-    const float* __restrict__ src_cov, const float* __restrict__ pose, float max_d2, float r0,
+    Grid g, Grid dg, int has_delta, float r0d, const float* __restrict__ map_cov, const float* __restrict__ src,
+    int64_t n, const float* __restrict__ src_cov, const float* __restrict__ pose, float max_d2, float r0,
     double* __restrict__ out, int32_t* __restrict__ corr, unsigned char* __restrict__ work) {
     __shared__ double red[GICP_THREADS / 32][GICP_STRIDE];
     __shared__ unsigned ticket;
@@ -223,12 +223,21 @@ __global__ void __launch_bounds__(GICP_THREADS) k_gicp_linearize(
                 float bd2 = INFINITY;
                 bool limited = false;
                 const int pos = nearest_within(g, px, py, pz, max_d2, r0, bd2, limited);
-                if (limited) atomicOr(g.status, ST_SEARCH_LIMIT);
+                float4 q = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
                 if (pos >= 0) {
-                    const float4 q = __ldg(&g.pts[pos]);
+                    q = __ldg(&g.pts[pos]);
                     pair = (int32_t)__float_as_uint(q.w);
-                    pair_terms(R, px, py, pz, q, map_cov + 6 * (int64_t)pair, src_cov + 6 * i, v);
                 }
+                if (has_delta) {  // appended points: the nearer of the two (main index on ties)
+                    float bd2d = INFINITY;
+                    const int posd = nearest_within(dg, px, py, pz, max_d2, r0d, bd2d, limited);
+                    if (posd >= 0 && (pos < 0 || __float_as_uint(bd2d) < __float_as_uint(bd2))) {
+                        q = __ldg(&dg.pts[posd]);
+                        pair = (int32_t)(g.m + (int64_t)__float_as_uint(q.w));
+                    }
+                }
+                if (limited) atomicOr(g.status, ST_SEARCH_LIMIT);
+                if (pair >= 0) pair_terms(R, px, py, pz, q, map_cov + 6 * (int64_t)pair, src_cov + 6 * i, v);
             } else {
                 atomicOr(g.status, ST_NONFINITE);
             }
@@ -391,7 +400,7 @@ size_t pc_gicp_work_size() {
 cudaError_t pc_launch_gicp_linearize(const pc_target_s* t, const float* map_cov, const float* src,
                                      int64_t n, const float* src_cov, const float* pose,
                                      float max_dist, double* out, int32_t* corr, void* work,
-                                     float r0, cudaStream_t s) {
+                                     float r0, float r0d, cudaStream_t s) {
     if (n == 0) return cudaMemsetAsync(out, 0, GICP_VALS * sizeof(double), s);
     const int maxb = gicp_max_blocks();
     if (maxb < 1) return cudaErrorInvalidDevice;
@@ -400,8 +409,10 @@ cudaError_t pc_launch_gicp_linearize(const pc_target_s* t, const float* map_cov,
     cudaError_t e = cudaMemsetAsync(work, 0, sizeof(unsigned), s);
     if (e != cudaSuccess) return e;
     const float max_d2 = max_dist * max_dist;
-    k_gicp_linearize<<<blocks, GICP_THREADS, 0, s>>>(t->g, map_cov, src, n, src_cov, pose, max_d2, r0,
-                                                     out, corr, static_cast<unsigned char*>(work));
+    const Grid dg = t->delta ? t->delta->g : t->g;
+    k_gicp_linearize<<<blocks, GICP_THREADS, 0, s>>>(t->g, dg, t->delta ? 1 : 0, r0d, map_cov, src, n, src_cov,
+                                                     pose, max_d2, r0, out, corr,
+                                                     static_cast<unsigned char*>(work));
     return cudaGetLastError();
 }
 

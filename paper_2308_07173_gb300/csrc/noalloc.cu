@@ -48,6 +48,7 @@ extern "C" pc_status pc_batch_run_noalloc(pc_target t, const pc_scan* scans, int
     if (!pc_target_is_live(t)) return PC_ERR_DESTROYED;
     if (!scans || n_scans < 1 || n_scans > PC_NOALLOC_MAX_SCANS) return PC_ERR_INVALID_ARG;
     if (k < 1 || k > 64 || !std::isfinite(eps)) return PC_ERR_INVALID_ARG;
+    if (t->delta) return PC_ERR_INVALID_ARG;  // appended points: pc_target_compact first
     if ((int64_t)k > t->g.m) return PC_ERR_K_GT_M;
     int prev = -1;
     if (cudaGetDevice(&prev) != cudaSuccess) return PC_ERR_CUDA;

@@ -59,7 +59,7 @@ pc_status check_target(const pc_target_s* t) {
 
 pc_status check_query_args(const pc_target_s* t, int64_t N, int k) {
     if (k < 1 || k > 64 || N < 0) return PC_ERR_INVALID_ARG;
-    if ((int64_t)k > t->g.m) return PC_ERR_K_GT_M;
+    if ((int64_t)k > t->g.m + t->delta_m) return PC_ERR_K_GT_M;
     if (N > ((int64_t)1 << 40)) return PC_ERR_INVALID_ARG;
     return PC_OK;
 }
@@ -150,6 +150,63 @@ size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
 }  // namespace
 
+// A target (grid + calibration) that is not yet a registered handle.
+static pc_status build_target_internal(const float* xyz, int64_t M, const pc_build_opts& o, cudaStream_t st,
+                                       pc_target_s** out) {
+    pc_target_s* t = new (std::nothrow) pc_target_s();
+    if (!t) return PC_ERR_OOM;
+    std::memset(t, 0, sizeof(*t));
+    t->magic = PC_MAGIC_LIVE;
+    cudaGetDevice(&t->device);
+    t->opts = o;
+    default_tune(&t->tune);
+    pc_status r = pc_build_grid(xyz, M, o, st, t);
+    if (r == PC_OK) r = calibrate_rho(t, st);
+    if (r != PC_OK) {
+        cudaStreamSynchronize(st);
+        pc_free_grid(t);
+        delete t;
+        return r;
+    }
+    *out = t;
+    return PC_OK;
+}
+
+static pc_status ensure_stage2(pc_target_s* t, size_t bytes) {
+    if (t->stage2_bytes >= bytes) return PC_OK;
+    if (t->stage2) cudaFree(t->stage2);
+    t->stage2 = nullptr;
+    t->stage2_bytes = 0;
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) return pc_from_cuda(e);
+    t->stage2 = p;
+    t->stage2_bytes = bytes;
+    return PC_OK;
+}
+
+// The search over the target as it stands: its grid, or its grid and the
+// delta grid of appended points merged.
+static pc_status launch_search(pc_target_s* t, const float* q, int64_t N, int k, float eps, int32_t* idx,
+                               float* d2, float* cov, cudaStream_t st) {
+    if (!t->delta) return pc_from_cuda(pc_launch_knn(t, q, N, k, eps, idx, d2, cov, pc_rho0(t, k), st));
+    const size_t need = pc_union_temp_bytes(t, N, k);
+    pc_status r = need ? ensure_stage2(t, need) : PC_OK;
+    if (r != PC_OK) return r;
+    return pc_from_cuda(pc_launch_knn_union(t, q, N, k, eps, idx, d2, cov, t->stage2, st));
+}
+
+static void free_delta(pc_target_s* t) {
+    if (t->delta) {
+        pc_free_grid(t->delta);
+        delete t->delta;
+        t->delta = nullptr;
+    }
+    if (t->delta_xyz) cudaFree(t->delta_xyz);
+    t->delta_xyz = nullptr;
+    t->delta_m = t->delta_cap = 0;
+}
+
 pc_status pc_from_cuda(cudaError_t e) {
     if (e == cudaSuccess) return PC_OK;
     cudaGetLastError();  // clear a non-sticky error
@@ -191,22 +248,9 @@ pc_status pc_build_target(const float* xyz_dev, int64_t M, const pc_build_opts* 
     if (o.occupancy <= 0) o.occupancy = 12.0f;
     if (o.hash_load <= 0 || o.hash_load > 0.9f) o.hash_load = 0.5f;
     if (o.max_box_cells <= 0) o.max_box_cells = 4096;
-    pc_target_s* t = new (std::nothrow) pc_target_s();
-    if (!t) return PC_ERR_OOM;
-    std::memset(t, 0, sizeof(*t));
-    t->magic = PC_MAGIC_LIVE;
-    cudaGetDevice(&t->device);
-    t->opts = o;
-    default_tune(&t->tune);
-    cudaStream_t st = (cudaStream_t)s;
-    pc_status r = pc_build_grid(xyz_dev, M, o, st, t);
-    if (r == PC_OK) r = calibrate_rho(t, st);
-    if (r != PC_OK) {
-        cudaStreamSynchronize(st);
-        pc_free_grid(t);
-        delete t;
-        return r;
-    }
+    pc_target_s* t = nullptr;
+    pc_status r = build_target_internal(xyz_dev, M, o, (cudaStream_t)s, &t);
+    if (r != PC_OK) return r;
     track(t);
     *out = t;
     return PC_OK;
@@ -216,6 +260,9 @@ void pc_destroy_target(pc_target t) {
     if (!t || !live(t)) return;
     untrack(t);
     DeviceGuard dg(t->device);
+    free_delta(t);
+    if (t->stage2) cudaFree(t->stage2);
+    t->stage2 = nullptr;
     pc_free_grid(t);
     t->magic = PC_MAGIC_DEAD;
     delete t;
@@ -253,8 +300,10 @@ pc_status pc_get_info(pc_target t, pc_target_info* info) {
     info->dims[0] = t->g.dimx;
     info->dims[1] = t->g.dimy;
     info->dims[2] = t->g.dimz;
-    info->device_bytes = t->device_bytes + (int64_t)t->stage_bytes;
+    info->device_bytes = t->device_bytes + (int64_t)t->stage_bytes + (int64_t)t->stage2_bytes +
+                         (t->delta ? t->delta->device_bytes : 0) + (int64_t)sizeof(float) * 3 * t->delta_cap;
     for (int i = 0; i < 64; ++i) info->rho_hint[i] = t->rho_hint[i];
+    info->delta_m = t->delta_m;
     return PC_OK;
 }
 
@@ -268,8 +317,7 @@ pc_status pc_knn(pc_target t, const float* q_dev, int64_t N, int k, int32_t* idx
     if (!is_device_ptr(q_dev) || !is_device_ptr(idx_dev) || !is_device_ptr(d2_dev))
         return PC_ERR_BAD_POINTER;
     DeviceGuard dg(t->device);
-    return pc_from_cuda(
-        pc_launch_knn(t, q_dev, N, k, -1.0f, idx_dev, d2_dev, nullptr, pc_rho0(t, k), (cudaStream_t)s));
+    return launch_search(t, q_dev, N, k, -1.0f, idx_dev, d2_dev, nullptr, (cudaStream_t)s);
 }
 
 pc_status pc_cov(pc_target t, const int32_t* idx_dev, int64_t N, int k, float eps, float* cov_dev,
@@ -281,6 +329,7 @@ pc_status pc_cov(pc_target t, const int32_t* idx_dev, int64_t N, int k, float ep
     if (!idx_dev || !cov_dev) return PC_ERR_INVALID_ARG;
     if (!is_device_ptr(idx_dev) || !is_device_ptr(cov_dev)) return PC_ERR_BAD_POINTER;
     DeviceGuard dg(t->device);
+    if (t->delta) return pc_from_cuda(pc_launch_cov_union(t, idx_dev, N, k, eps, cov_dev, (cudaStream_t)s));
     return pc_from_cuda(pc_launch_cov(t, idx_dev, N, k, eps, cov_dev, (cudaStream_t)s));
 }
 
@@ -296,8 +345,7 @@ pc_status pc_knn_cov(pc_target t, const float* q_dev, int64_t N, int k, float ep
         !is_device_ptr(cov_dev))
         return PC_ERR_BAD_POINTER;
     DeviceGuard dg(t->device);
-    return pc_from_cuda(pc_launch_knn(t, q_dev, N, k, eps, idx_dev, d2_dev, cov_dev, pc_rho0(t, k),
-                                      (cudaStream_t)s));
+    return launch_search(t, q_dev, N, k, eps, idx_dev, d2_dev, cov_dev, (cudaStream_t)s);
 }
 
 pc_status pc_knn_cov_host(pc_target t, const float* q_host, int64_t N, int k, float eps,
@@ -319,7 +367,10 @@ pc_status pc_knn_cov_host(pc_target t, const float* q_host, int64_t N, int k, fl
     float* cov = reinterpret_cast<float*>(base + bq + bi + bd);
     cudaStream_t st = (cudaStream_t)s;
     cudaError_t e = cudaMemcpyAsync(q, q_host, sizeof(float) * 3 * N, cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = pc_launch_knn(t, q, N, k, eps, idx, d2, cov, pc_rho0(t, k), st);
+    if (e == cudaSuccess) {
+        r = launch_search(t, q, N, k, eps, idx, d2, cov, st);
+        if (r != PC_OK) return r;
+    }
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(idx_host, idx, sizeof(int32_t) * N * k, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess)
@@ -363,6 +414,7 @@ pc_status pc_batch_plan(pc_target t, const pc_scan* scans, int n_scans, int k, f
     pc_status r = check_target(t);
     if (r != PC_OK) return r;
     if (!scans || n_scans < 1 || k < 1 || k > 64 || !std::isfinite(eps)) return PC_ERR_INVALID_ARG;
+    if (t->delta) return PC_ERR_INVALID_ARG;  // appended points: pc_target_compact first
     if ((int64_t)k > t->g.m) return PC_ERR_K_GT_M;
     bool any_cov = false;
     for (int i = 0; i < n_scans; ++i) {
@@ -426,6 +478,7 @@ pc_status pc_batch_run(pc_batch b, pc_stream s) {
     if (!b) return PC_ERR_INVALID_ARG;
     if (!live(b)) return PC_ERR_DESTROYED;
     if (!live(b->t)) return PC_ERR_DESTROYED;
+    if (b->t->delta || b->t->g.table != b->g.table) return PC_ERR_INVALID_ARG;  // the target changed since planning
     if (b->total_tiles == 0) return PC_OK;
     DeviceGuard dg(b->t->device);
     cudaStream_t st = (cudaStream_t)s;
@@ -474,6 +527,7 @@ pc_status pc_batch_run_scratch(pc_target t, const pc_scan* scans, int n_scans, i
     pc_status r = check_target(t);
     if (r != PC_OK) return r;
     if (!scans || n_scans < 1 || k < 1 || k > 64 || !std::isfinite(eps)) return PC_ERR_INVALID_ARG;
+    if (t->delta) return PC_ERR_INVALID_ARG;  // appended points: pc_target_compact first
     if ((int64_t)k > t->g.m) return PC_ERR_K_GT_M;
     if (!scratch_dev || (reinterpret_cast<uintptr_t>(scratch_dev) & 255u) ||
         scratch_bytes < pc_batch_scratch_bytes(n_scans))
@@ -542,23 +596,21 @@ static int host_cell_of(float v, float o, float inv_h) {
     return (int)t;
 }
 
-pc_status pc_set_window(pc_target t, const pc_window* w) {
-    pc_status r = check_target(t);
-    if (r != PC_OK) return r;
-    pcdev::Grid& g = t->g;
-    if (!w) {
-        pc_clear_window(g);
-        return PC_OK;
-    }
-    for (int a = 0; a < 3; ++a)
-        if (std::isnan(w->lo[a]) || std::isnan(w->hi[a]) || !(w->lo[a] <= w->hi[a]))
-            return PC_ERR_INVALID_ARG;
+// The window of t->win onto one grid (the main one or the delta's).
+static void apply_window(const pc_target_s* t, pcdev::Grid& g, const float* bbox_max) {
+    pc_clear_window(g);
+    if (!t->has_win) return;
+    const pc_window* w = &t->win;
     const float o[3] = {g.ox, g.oy, g.oz};
     const int dim[3] = {g.dimx, g.dimy, g.dimz};
-    int lo[3], hi[3];
+    int lo[3], hi[3], tl[3], th[3];
     for (int a = 0; a < 3; ++a) {
         lo[a] = std::max(host_cell_of(w->lo[a], o[a], g.inv_h), 0);
         hi[a] = std::min(host_cell_of(w->hi[a], o[a], g.inv_h), dim[a] - 1);
+        // boundary cells whose points can fall outside the box: only where
+        // the bound lies inside the grid's bounding box [origin, bbox_max]
+        tl[a] = w->lo[a] > o[a] ? lo[a] : -1;
+        th[a] = w->hi[a] < bbox_max[a] ? hi[a] : -1;
     }
     g.windowed = 1;
     g.wlx = lo[0];
@@ -567,13 +619,6 @@ pc_status pc_set_window(pc_target t, const pc_window* w) {
     g.why = hi[1];
     g.wlz = lo[2];
     g.whz = hi[2];
-    // boundary cells whose points can fall outside the box: only where the
-    // bound lies inside the target's bounding box [origin, bbox_max]
-    int tl[3], th[3];
-    for (int a = 0; a < 3; ++a) {
-        tl[a] = w->lo[a] > o[a] ? lo[a] : -1;
-        th[a] = w->hi[a] < t->bbox_max[a] ? hi[a] : -1;
-    }
     g.tlx = tl[0];
     g.thx = th[0];
     g.tly = tl[1];
@@ -586,6 +631,111 @@ pc_status pc_set_window(pc_target t, const pc_window* w) {
     g.whix = w->hi[0];
     g.whiy = w->hi[1];
     g.whiz = w->hi[2];
+}
+
+pc_status pc_set_window(pc_target t, const pc_window* w) {
+    pc_status r = check_target(t);
+    if (r != PC_OK) return r;
+    if (w)
+        for (int a = 0; a < 3; ++a)
+            if (std::isnan(w->lo[a]) || std::isnan(w->hi[a]) || !(w->lo[a] <= w->hi[a]))
+                return PC_ERR_INVALID_ARG;
+    t->has_win = w ? 1 : 0;
+    if (w) t->win = *w;
+    apply_window(t, t->g, t->bbox_max);
+    if (t->delta) apply_window(t, t->delta->g, t->delta->bbox_max);
+    return PC_OK;
+}
+
+pc_status pc_target_append(pc_target t, const float* xyz_dev, int64_t n, pc_stream s) {
+    pc_status r = check_target(t);
+    if (r != PC_OK) return r;
+    if (n < 0) return PC_ERR_INVALID_ARG;
+    if (n == 0) return PC_OK;
+    if (!xyz_dev) return PC_ERR_INVALID_ARG;
+    if (!is_device_ptr(xyz_dev)) return PC_ERR_BAD_POINTER;
+    const int64_t tot = t->delta_m + n;
+    if (t->g.m + tot >= ((int64_t)1 << 31)) return PC_ERR_INVALID_ARG;
+    DeviceGuard dg(t->device);
+    cudaStream_t st = (cudaStream_t)s;
+    if (tot > t->delta_cap) {  // grow the appended-points array (doubling)
+        const int64_t cap = std::max<int64_t>(tot, 2 * t->delta_cap);
+        float* p = nullptr;
+        cudaError_t e = cudaMalloc(&p, sizeof(float) * 3 * cap);
+        if (e != cudaSuccess) return pc_from_cuda(e);
+        if (t->delta_m > 0)
+            e = cudaMemcpyAsync(p, t->delta_xyz, sizeof(float) * 3 * t->delta_m, cudaMemcpyDeviceToDevice, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) {
+            cudaFree(p);
+            return pc_from_cuda(e);
+        }
+        if (t->delta_xyz) cudaFree(t->delta_xyz);
+        t->delta_xyz = p;
+        t->delta_cap = cap;
+    }
+    cudaError_t e = cudaMemcpyAsync(t->delta_xyz + 3 * t->delta_m, xyz_dev, sizeof(float) * 3 * n,
+                                    cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) return pc_from_cuda(e);
+    // the delta grid over every appended point (the main grid is untouched)
+    pc_target_s* d = nullptr;
+    r = build_target_internal(t->delta_xyz, tot, t->opts, st, &d);
+    if (r != PC_OK) return r;  // e.g. a non-finite point: nothing appended
+    d->tune = t->tune;
+    d->g.status = t->g.status;  // conditions of the delta search report on the handle
+    d->g.stats = t->g.stats;
+    if (t->delta) {
+        pc_free_grid(t->delta);
+        delete t->delta;
+    }
+    t->delta = d;
+    t->delta_m = tot;
+    apply_window(t, d->g, d->bbox_max);
+    return PC_OK;
+}
+
+pc_status pc_target_compact(pc_target t, pc_stream s) {
+    pc_status r = check_target(t);
+    if (r != PC_OK) return r;
+    if (!t->delta) return PC_OK;
+    DeviceGuard dg(t->device);
+    cudaStream_t st = (cudaStream_t)s;
+    const int64_t tot = t->g.m + t->delta_m;
+    float* all = nullptr;
+    cudaError_t e = cudaMalloc(&all, sizeof(float) * 3 * tot);
+    if (e != cudaSuccess) return pc_from_cuda(e);
+    e = pc_launch_pack_xyz(t, all, st);
+    pc_target_s* n = nullptr;
+    if (e == cudaSuccess) r = build_target_internal(all, tot, t->opts, st, &n);
+    else r = pc_from_cuda(e);
+    cudaStreamSynchronize(st);
+    cudaFree(all);
+    if (r != PC_OK) return r;
+    // the handle keeps its identity and settings; its grid is the new one
+    pc_free_grid(t);
+    t->g = n->g;
+    t->bbox_max[0] = n->bbox_max[0];
+    t->bbox_max[1] = n->bbox_max[1];
+    t->bbox_max[2] = n->bbox_max[2];
+    std::memcpy(t->rho_hint, n->rho_hint, sizeof(t->rho_hint));
+    t->table_cap = n->table_cap;
+    t->device_bytes = n->device_bytes;
+    t->table = n->table;
+    t->pts = n->pts;
+    t->xyz = n->xyz;
+    t->cell_keys = n->cell_keys;
+    t->cell_start = n->cell_start;
+    t->occ = n->occ;
+    t->rank = n->rank;
+    t->status = n->status;
+    delete n;  // its buffers now belong to t
+    free_delta(t);
+    apply_window(t, t->g, t->bbox_max);
+    if (t->ck.type != 0) {  // the polynomial/HI origin follows the new bounding box
+        t->ck.ox = t->g.ox;
+        t->ck.oy = t->g.oy;
+        t->ck.oz = t->g.oz;
+    }
     return PC_OK;
 }
 
@@ -656,8 +806,13 @@ pc_status pc_gicp_linearize(pc_target map, const float* map_cov_dev, const float
     // start radius: the calibrated distance to the nearest other map point
     float r0 = pc_rho0(map, map->g.m >= 2 ? 2 : 1);
     if (!(r0 > 0.0f)) r0 = map->g.h;
+    float r0d = r0;
+    if (map->delta) {
+        r0d = pc_rho0(map->delta, map->delta->g.m >= 2 ? 2 : 1);
+        if (!(r0d > 0.0f)) r0d = map->delta->g.h;
+    }
     return pc_from_cuda(pc_launch_gicp_linearize(map, map_cov_dev, src_dev, n, src_cov_dev, pose_dev,
-                                                 max_dist, out_dev, corr_dev, work_dev, r0,
+                                                 max_dist, out_dev, corr_dev, work_dev, r0, r0d,
                                                  (cudaStream_t)s));
 }
 

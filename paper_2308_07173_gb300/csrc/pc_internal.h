@@ -54,6 +54,18 @@ struct pc_target_s {
     void* stage;
     size_t stage_bytes;
     CovKernel ck;  // covariance weights (type 0: none)
+    // incremental updates (pc_target_append): the appended points, f32
+    // [delta_m, 3] in append order, and a grid over them; their indices
+    // follow the main map's (M + position)
+    pc_target_s* delta;
+    float* delta_xyz;
+    int64_t delta_m, delta_cap;
+    // the window of pc_set_window, kept to re-apply to a rebuilt delta grid
+    pc_window win;
+    int has_win;
+    // staging for the merge of main and delta searches, grown on demand
+    void* stage2;
+    size_t stage2_bytes;
 };
 
 struct pc_batch_s {
@@ -124,9 +136,17 @@ size_t pc_gicp_work_size();
 cudaError_t pc_launch_gicp_linearize(const pc_target_s* t, const float* map_cov, const float* src,
                                      int64_t n, const float* src_cov, const float* pose,
                                      float max_dist, double* out, int32_t* corr, void* work,
-                                     float r0, cudaStream_t s);
+                                     float r0, float r0d, cudaStream_t s);
 cudaError_t pc_launch_gicp_update(const double* lin, float lambda, float* pose, double* xi,
                                   cudaStream_t s);
+
+// delta.cu: searches over the main grid plus the delta grid
+cudaError_t pc_launch_knn_union(const pc_target_s* t, const float* q, int64_t N, int k, float eps,
+                                int32_t* idx, float* d2, float* cov, void* temp, cudaStream_t s);
+size_t pc_union_temp_bytes(const pc_target_s* t, int64_t N, int k);
+cudaError_t pc_launch_cov_union(const pc_target_s* t, const int32_t* idx, int64_t N, int k, float eps,
+                                float* cov, cudaStream_t s);
+cudaError_t pc_launch_pack_xyz(const pc_target_s* t, float* out, cudaStream_t s);
 
 // cov_weighted.cu
 cudaError_t pc_launch_cov_weighted(const pcdev::Grid& g, const CovKernel& ck, const float* q,

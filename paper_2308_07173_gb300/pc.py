@@ -106,6 +106,7 @@ class pc_target_info(ctypes.Structure):
         ("dims", ctypes.c_int * 3),
         ("device_bytes", ctypes.c_int64),
         ("rho_hint", ctypes.c_float * 64),
+        ("delta_m", ctypes.c_int64),
     ]
 
 
@@ -145,6 +146,8 @@ SIGNATURES = {
     "pc_batch_scratch_bytes": (ctypes.c_size_t, [_INT]),
     "pc_batch_run_scratch": (_INT, [_VP, ctypes.POINTER(pc_scan), _INT, _INT, _F, _VP, ctypes.c_size_t, _VP]),
     "pc_set_window": (_INT, [_VP, ctypes.POINTER(pc_window)]),
+    "pc_target_append": (_INT, [_VP, _VP, _I64, _VP]),
+    "pc_target_compact": (_INT, [_VP, _VP]),
     "pc_set_cov_kernel": (_INT, [_VP, ctypes.POINTER(pc_cov_kernel)]),
     "pc_wall_default_opts": (None, [ctypes.POINTER(pc_wall_opts)]),
     "pc_wall_create": (_INT, [_I64, ctypes.POINTER(pc_wall_opts), ctypes.POINTER(_VP)]),
@@ -375,6 +378,7 @@ class Target:
             "dims": list(i.dims),
             "device_bytes": i.device_bytes,
             "rho_hint": list(i.rho_hint),
+            "delta_m": i.delta_m,
         }
 
     def set_tune(self, tile: int = 0, warps: int = 0, rho_scale: float = 0.0, order: int = 0):
@@ -439,6 +443,19 @@ class Target:
         'laplacian'); 'none' restores the plain covariance."""
         _check(pc_set_cov_kernel(self.handle, kernel, sigma, alpha, c, d), "pc_set_cov_kernel")
 
+    def append(self, xyz, stream=None):
+        """Add points to the map without rebuilding its grid (indices continue
+        after the existing ones)."""
+        torch = _torch()
+        xyz = _dev_tensor(xyz, torch.float32, 3, "xyz")
+        _check(load().pc_target_append(self.handle, xyz.data_ptr(), xyz.shape[0], _stream_handle(stream)),
+               "pc_target_append")
+        self.m_appended = getattr(self, "m_appended", 0) + xyz.shape[0]
+
+    def compact(self, stream=None):
+        """Fold appended points into a rebuilt main grid."""
+        _check(load().pc_target_compact(self.handle, _stream_handle(stream)), "pc_target_compact")
+
     def set_window(self, lo=None, hi=None):
         """Restrict later searches to the map points in the box [lo, hi]
         (sliding-window submap); no arguments restore the whole map."""
@@ -467,8 +484,8 @@ class Target:
         if pose.numel() != 12:
             raise ValueError("pose must hold 12 floats (R row-major, t)")
         n = src.shape[0]
-        if map_cov.shape[0] != self.m or src_cov.shape[0] != n:
-            raise ValueError("map_cov must be [M,6] for this target and src_cov [n,6] for src")
+        if map_cov.shape[0] != self.m + getattr(self, "m_appended", 0) or src_cov.shape[0] != n:
+            raise ValueError("map_cov must be [M,6] for this target (appended points included) and src_cov [n,6]")
         out = out if out is not None else torch.empty(PC_GICP_OUT, dtype=torch.float64, device=src.device)
         work = work if work is not None else self.gicp_work()
         cp = corr.data_ptr() if corr is not None else None
