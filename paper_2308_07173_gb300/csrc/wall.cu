@@ -233,42 +233,45 @@ __device__ void uf_union(int* parent, int a, int b, uint32_t cap, int* err) {
     atomicOr(err, WALL_ERR_LIMIT);
 }
 
-// Visits the vertical voxels linked to v (d2 <= tol^2) with smaller index.
+// Visits the vertical voxels linked to v (d2 <= tol^2) with smaller index
+// that lie in neighbour cell `c` (0..26) of v's cluster cell.
 template <typename F>
-__device__ __forceinline__ void for_links_below(const float4* __restrict__ cent, uint32_t v, uint32_t nv,
-                                                const WallParams& P, const u64* __restrict__ ckeys,
-                                                const int* __restrict__ head, const int* __restrict__ next, F&& f) {
-    const float4 c = cent[v];
-    const u64 k0 = cluster_key(c, P.inv_c);
+__device__ __forceinline__ void for_links_in_cell(const float4* __restrict__ cent, uint32_t v, uint32_t nv,
+                                                  int c, const WallParams& P, const u64* __restrict__ ckeys,
+                                                  const int* __restrict__ head, const int* __restrict__ next,
+                                                  F&& f) {
+    const float4 cv = cent[v];
+    const u64 k0 = cluster_key(cv, P.inv_c);
     const long long a0 = (long long)(k0 & 0x1fffffull), b0 = (long long)((k0 >> 21) & 0x1fffffull),
                     d0 = (long long)(k0 >> 42);
-    for (int dz = -1; dz <= 1; ++dz)
-        for (int dy = -1; dy <= 1; ++dy)
-            for (int dx = -1; dx <= 1; ++dx) {
-                const u64 key = ((u64)(a0 + dx) & 0x1fffffull) | (((u64)(b0 + dy) & 0x1fffffull) << 21) |
-                                (((u64)(d0 + dz) & 0x1fffffull) << 42);
-                const int s = hash_find(ckeys, P.log2cap, key);
-                if (s < 0) continue;
-                int j = head[s];
-                for (uint32_t it = 0; j >= 0 && it <= nv; ++it) {
-                    if ((uint32_t)j < v && sqdist3(c, cent[j]) <= P.tol2) f(j);
-                    j = next[j];
-                }
-            }
+    const int dx = c % 3 - 1, dy = (c / 3) % 3 - 1, dz = c / 9 - 1;
+    const u64 key = ((u64)(a0 + dx) & 0x1fffffull) | (((u64)(b0 + dy) & 0x1fffffull) << 21) |
+                    (((u64)(d0 + dz) & 0x1fffffull) << 42);
+    const int s = hash_find(ckeys, P.log2cap, key);
+    if (s < 0) return;
+    int j = head[s];
+    for (uint32_t it = 0; j >= 0 && it <= nv; ++it) {
+        if ((uint32_t)j < v && sqdist3(cv, cent[j]) <= P.tol2) f(j);
+        j = next[j];
+    }
 }
 
 // 3a. every vertical voxel starts under its smallest linked neighbour (a
 // valid forest: parents are smaller members of the same component), so the
-// unions that follow mostly find their ends already joined
+// unions that follow mostly find their ends already joined.  One warp per
+// voxel, one lane per neighbouring cell: the 27 list walks run side by side.
 __global__ void k_wall_link_init(const float4* __restrict__ cent, const uint32_t* __restrict__ nvp, WallParams P,
                                  const int* __restrict__ vertical, const u64* __restrict__ ckeys,
                                  const int* __restrict__ head, const int* __restrict__ next, int* parent) {
     const uint32_t nv = *nvp;
-    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < nv; v += gridDim.x * blockDim.x) {
-        if (!vertical[v]) continue;
+    const int lane = threadIdx.x & 31;
+    const uint32_t wpb = blockDim.x >> 5;
+    for (uint32_t v = blockIdx.x * wpb + (threadIdx.x >> 5); v < nv; v += gridDim.x * wpb) {
+        if (!vertical[v]) continue;  // warp-uniform
         int m = (int)v;
-        for_links_below(cent, v, nv, P, ckeys, head, next, [&](int j) { m = j < m ? j : m; });
-        parent[v] = m;
+        if (lane < 27) for_links_in_cell(cent, v, nv, lane, P, ckeys, head, next, [&](int j) { m = j < m ? j : m; });
+        for (int o = 16; o > 0; o >>= 1) m = min(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if (lane == 0) parent[v] = m;
     }
 }
 
@@ -287,26 +290,22 @@ __global__ void k_wall_jump(const uint32_t* __restrict__ nvp, const int* __restr
 }
 constexpr int JUMP_ROUNDS = 12;
 
-// 3. links between vertical voxels in the 27 neighbouring cluster cells
+// 3. links between vertical voxels in the 27 neighbouring cluster cells:
+// one warp per voxel, one lane per cell; pairs already under one parent are
+// joined, the rest go through the union-find
 __global__ void k_wall_union(const float4* __restrict__ cent, const uint32_t* __restrict__ nvp, WallParams P,
                              const int* __restrict__ vertical, const u64* __restrict__ ckeys,
                              const int* __restrict__ head, const int* __restrict__ next, int* parent, int* err) {
     const uint32_t nv = *nvp;
-    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < nv; v += gridDim.x * blockDim.x) {
-        if (!vertical[v]) continue;
-        // pairs already under one parent are joined; the walk only collects
-        // the rest (plain loads, so the list walks overlap), and the unions
-        // with their root chases run after it
+    const int lane = threadIdx.x & 31;
+    const uint32_t wpb = blockDim.x >> 5;
+    for (uint32_t v = blockIdx.x * wpb + (threadIdx.x >> 5); v < nv; v += gridDim.x * wpb) {
+        if (!vertical[v]) continue;  // warp-uniform
+        if (lane >= 27) continue;
         const int pv = __ldcg(&parent[v]);
-        int pend[8];
-        int np = 0;
-        for_links_below(cent, v, nv, P, ckeys, head, next, [&](int j) {
-            if (__ldcg(&parent[j]) != pv) {
-                if (np < 8) pend[np++] = j;
-                else uf_union(parent, (int)v, j, nv, err);
-            }
+        for_links_in_cell(cent, v, nv, lane, P, ckeys, head, next, [&](int j) {
+            if (__ldcg(&parent[j]) != pv) uf_union(parent, (int)v, j, nv, err);
         });
-        for (int i = 0; i < np; ++i) uf_union(parent, (int)v, pend[i], nv, err);
     }
 }
 
@@ -644,10 +643,12 @@ pc_status pc_wall_detect(pc_wall w, const float* pts_dev, int64_t n, pc_stream s
         k_wall_vote<<<vb, NT, 0, st>>>(w->cent, w->nv, P, w->vkeys, w->vcount, w->err);
         k_wall_vertical<<<vb, NT, 0, st>>>(w->cent, w->nv, P, w->vkeys, w->vcount, w->vertical, w->parent,
                                           w->ckeys, w->head, w->next, w->nvert, w->err);
-        k_wall_link_init<<<vb, NT, 0, st>>>(w->cent, w->nv, P, w->vertical, w->ckeys, w->head, w->next,
+        // one warp per voxel for the list walks
+        const unsigned wb = blocks_for(n * 32, NT);
+        k_wall_link_init<<<wb, NT, 0, st>>>(w->cent, w->nv, P, w->vertical, w->ckeys, w->head, w->next,
                                            w->parent);
         for (int r = 0; r < JUMP_ROUNDS; ++r) k_wall_jump<<<vb, NT, 0, st>>>(w->nv, w->vertical, w->parent);
-        k_wall_union<<<vb, NT, 0, st>>>(w->cent, w->nv, P, w->vertical, w->ckeys, w->head, w->next, w->parent,
+        k_wall_union<<<wb, NT, 0, st>>>(w->cent, w->nv, P, w->vertical, w->ckeys, w->head, w->next, w->parent,
                                        w->err);
         k_wall_label<<<vb, NT, 0, st>>>(w->cent, w->nv, w->vertical, w->parent, w->label, w->cmin_x, w->cmax_x,
                                        w->cmin_y, w->cmax_y, w->ccount, w->err);
