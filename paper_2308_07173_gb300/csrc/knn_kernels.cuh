@@ -341,6 +341,19 @@ __host__ __device__ float3 min_eigvec(float a00, float a01, float a02, float a11
 // by k.  Built with --fmad=false, so every + and * below is rounded once;
 // every caller runs this same code on the same values, so the fused kernel
 // and pc_cov agree bit for bit.
+// The six packed entries of one covariance row: three 8-byte stores when
+// the row is 8-byte aligned (every row of an aligned [N,6] array is).
+__device__ __forceinline__ void store6(float* out, float a, float b, float c, float d, float e, float f) {
+    if ((reinterpret_cast<uintptr_t>(out) & 7) == 0) {
+        float2* o2 = reinterpret_cast<float2*>(out);
+        o2[0] = make_float2(a, b);
+        o2[1] = make_float2(c, d);
+        o2[2] = make_float2(e, f);
+    } else {
+        out[0] = a; out[1] = b; out[2] = c; out[3] = d; out[4] = e; out[5] = f;
+    }
+}
+
 template <typename G>
 __device__ __forceinline__ void cov_core(G&& get, int k, float eps, float* out) {
     const float4 p0 = get(0);
@@ -369,17 +382,13 @@ __device__ __forceinline__ void cov_core(G&& get, int k, float eps, float* out) 
     cxx = cxx / fk; cxy = cxy / fk; cxz = cxz / fk;
     cyy = cyy / fk; cyz = cyz / fk; czz = czz / fk;
     if (eps < 0.0f) {
-        out[0] = cxx; out[1] = cxy; out[2] = cxz; out[3] = cyy; out[4] = cyz; out[5] = czz;
+        store6(out, cxx, cxy, cxz, cyy, cyz, czz);
         return;
     }
     const float3 n = min_eigvec(cxx, cxy, cxz, cyy, cyz, czz);
     const float f = 1.0f - eps;
-    out[0] = 1.0f - f * n.x * n.x;
-    out[1] = -f * n.x * n.y;
-    out[2] = -f * n.x * n.z;
-    out[3] = 1.0f - f * n.y * n.y;
-    out[4] = -f * n.y * n.z;
-    out[5] = 1.0f - f * n.z * n.z;
+    store6(out, 1.0f - f * n.x * n.x, -f * n.x * n.y, -f * n.x * n.z, 1.0f - f * n.y * n.y, -f * n.y * n.z,
+           1.0f - f * n.z * n.z);
 }
 
 __device__ __forceinline__ void nan_row(float* out) {
@@ -624,14 +633,52 @@ __device__ void lane_tile(const Grid& g, const float* __restrict__ q, int64_t n0
 #pragma unroll
         for (int r = 0; r < 32; ++r)
             if (r < k) P[r] = posl[(K[r] & (CAP - 1)) * 32 + lane];
+        // Each lane writes its own row, so every store instruction touches
+        // 32 rows; a row of 4j (2j) entries on a 16- (8-) byte aligned base is
+        // whole vectors, which takes a quarter (half) of the instructions.
+        const uintptr_t ab = reinterpret_cast<uintptr_t>(idx) | reinterpret_cast<uintptr_t>(d2);
+        const int vw = ((k & 3) == 0 && (ab & 15) == 0) ? 4 : (((k & 1) == 0 && (ab & 7) == 0) ? 2 : 1);
+        auto entry = [&](int r, int& iv, float& dv) {
+            posl[r * 32 + lane] = P[r];
+            const float4 p = __ldg(&g.pts[P[r]]);
+            iv = (int)__float_as_uint(p.w);
+            dv = sqdist_pinned(qx, qy, qz, p.x, p.y, p.z);
+        };
+        if (vw == 4) {
 #pragma unroll
-        for (int r = 0; r < 32; ++r)
-            if (r < k) {
-                posl[r * 32 + lane] = P[r];
-                const float4 p = __ldg(&g.pts[P[r]]);
-                idx[n * k + r] = (int32_t)__float_as_uint(p.w);
-                d2[n * k + r] = sqdist_pinned(qx, qy, qz, p.x, p.y, p.z);
-            }
+            for (int r = 0; r < 32; r += 4)
+                if (r < k) {
+                    int4 iv;
+                    float4 dv;
+                    entry(r, iv.x, dv.x);
+                    entry(r + 1, iv.y, dv.y);
+                    entry(r + 2, iv.z, dv.z);
+                    entry(r + 3, iv.w, dv.w);
+                    *reinterpret_cast<int4*>(idx + n * k + r) = iv;
+                    *reinterpret_cast<float4*>(d2 + n * k + r) = dv;
+                }
+        } else if (vw == 2) {
+#pragma unroll
+            for (int r = 0; r < 32; r += 2)
+                if (r < k) {
+                    int2 iv;
+                    float2 dv;
+                    entry(r, iv.x, dv.x);
+                    entry(r + 1, iv.y, dv.y);
+                    *reinterpret_cast<int2*>(idx + n * k + r) = iv;
+                    *reinterpret_cast<float2*>(d2 + n * k + r) = dv;
+                }
+        } else {
+#pragma unroll
+            for (int r = 0; r < 32; ++r)
+                if (r < k) {
+                    int iv;
+                    float dv;
+                    entry(r, iv, dv);
+                    idx[n * k + r] = iv;
+                    d2[n * k + r] = dv;
+                }
+        }
     } else if (active && !finite) {
         for (int r = 0; r < k; ++r) {
             idx[n * k + r] = -1;
