@@ -20,8 +20,8 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libpc.so")
 
-SOURCES = ["pc_api.cu", "grid_build.cu", "knn_cov.cu", "knn_window.cu", "noalloc.cu", "gicp.cu",
-           "cov_weighted.cu", "wall.cu", "delta.cu"]
+SOURCES = ["knn_cov.cu", "knn_window.cu", "knn_union.cu", "knn_union_win.cu", "pc_api.cu", "grid_build.cu",
+           "noalloc.cu", "gicp.cu", "cov_weighted.cu", "wall.cu", "delta.cu"]
 HEADERS = ["pc_device.cuh", "pc_internal.h", "pc_search.cuh", "knn_kernels.cuh", "cov_weighted.cuh"]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -53,6 +53,8 @@ cudaError_t ensure_attrs() {
     if (g_attr_done & bit) return cudaSuccess;
     if ((e = allow_all_smem<false>()) != cudaSuccess) return e;
     if ((e = pc_knn_win_attrs()) != cudaSuccess) return e;
+    if ((e = pc_knn_union_attrs()) != cudaSuccess) return e;
+    if ((e = pc_knn_union_win_attrs()) != cudaSuccess) return e;
     g_attr_done |= bit;
     return cudaSuccess;
 }
@@ -93,6 +95,32 @@ cudaError_t pc_launch_knn(const pc_target_s* t, const float* q, int64_t N, int k
         return cudaLaunchKernel(kern, dim3((unsigned)blocks), dim3(warps * 32), args, smem, s);
     });
     if (e == cudaSuccess && weighted) e = pc_launch_cov_weighted(g, t->ck, q, idx, N, k, eps, cov, s);
+    return e;
+}
+
+// The union search (a target with appended points): the same launch shape
+// as pc_launch_knn over the main grid and the delta grid together.
+cudaError_t pc_launch_knn_union(const pc_target_s* t, const float* q, int64_t N, int k, float eps,
+                                int32_t* idx, float* d2, float* cov, float rho0, cudaStream_t s) {
+    if (N == 0) return cudaSuccess;
+    cudaError_t e = ensure_attrs();
+    if (e != cudaSuccess) return e;
+    const int tile = clamp_tile(t->tune.tile);
+    const int warps = clamp_warps(t->tune.warps);
+    TileArgs a{k, eps, t->tune.rho_scale > 0 ? t->tune.rho_scale : 0.9f, t->tune.order == 0 ? 1 : 0};
+    const bool weighted = cov != nullptr && t->ck.type != 0;
+    const bool with_cov = cov != nullptr && !weighted;
+    const int mode = search_mode(k);
+    const size_t smem = (size_t)warps * warp_smem_bytes(mode);
+    const int64_t tiles = (N + tile - 1) / tile;
+    const int64_t blocks = (tiles + warps - 1) / warps;
+    Grid g = t->g;
+    Grid dg = t->delta->g;
+    float* covp = with_cov ? cov : nullptr;
+    void* args[] = {&g, &dg, (void*)&q, (void*)&N, (void*)&tile, &a, &rho0, &idx, &d2, &covp};
+    void* kern = g.windowed ? pc_knn_union_kernel_win(mode, with_cov) : pc_knn_union_kernel(mode, with_cov);
+    e = cudaLaunchKernel(kern, dim3((unsigned)blocks), dim3(warps * 32), args, smem, s);
+    if (e == cudaSuccess && weighted) e = pc_launch_cov_weighted_union(t, q, idx, N, k, eps, cov, s);
     return e;
 }
 

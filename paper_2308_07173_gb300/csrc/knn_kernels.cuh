@@ -120,11 +120,14 @@ __device__ __forceinline__ void flush(SearchState<SLOTS>& S, u64* pend, int k, i
 
 // One pass over up to 32 point ranges (one per lane): every point becomes a
 // candidate, 32 per step, each lane finding its owning range by a binary
-// search over the warp's exclusive prefix of counts.
+// search over the warp's exclusive prefix of counts.  Keys carry the point's
+// index plus ibase (the appended-points grid numbers its points after the
+// main grid's).
 template <int SLOTS>
 __device__ __forceinline__ void scan_ranges(const Grid& g, float qx, float qy, float qz,
                                             uint32_t start, uint32_t cnt, float tau,
-                                            SearchState<SLOTS>& S, u64* pend, int k, int lane) {
+                                            SearchState<SLOTS>& S, u64* pend, int k, int lane,
+                                            uint32_t ibase) {
     uint32_t incl = cnt;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -148,7 +151,7 @@ __device__ __forceinline__ void scan_ranges(const Grid& g, float qx, float qy, f
         if (t < total) {
             const float4 p = __ldg(&g.pts[st + (t - ej)]);
             const float d2 = sqdist_pinned(qx, qy, qz, p.x, p.y, p.z);
-            key = ((u64)__float_as_uint(d2) << 32) | (u64)__float_as_uint(p.w);
+            key = ((u64)__float_as_uint(d2) << 32) | (u64)(__float_as_uint(p.w) + ibase);
             pass = (d2 <= tau) && (key < S.kth) && (!g.windowed || in_window(g, p));
         }
         offer(S, pass, key, pend, k, lane);
@@ -184,7 +187,7 @@ __device__ __forceinline__ float cell_lower_bound2(const Grid& g, float qx, floa
 template <int SLOTS>
 __device__ void scan_box(const Grid& g, float qx, float qy, float qz, int lx, int ly, int lz,
                          int ex, int ey, int ez, float tau, SearchState<SLOTS>& S, u64* pend,
-                         int k, int lane) {
+                         int k, int lane, uint32_t ibase) {
     const int ncl = ex * ey * ez;
     for (int base = 0; base < ncl; base += 32) {
         const int c = base + lane;
@@ -198,13 +201,13 @@ __device__ void scan_box(const Grid& g, float qx, float qy, float qz, int lx, in
             start = v.x;
             cnt = v.y;
         }
-        scan_ranges(g, qx, qy, qz, start, cnt, tau, S, pend, k, lane);
+        scan_ranges(g, qx, qy, qz, start, cnt, tau, S, pend, k, lane, ibase);
     }
 }
 
 template <int SLOTS>
 __device__ void scan_all_cells(const Grid& g, float qx, float qy, float qz, SearchState<SLOTS>& S,
-                               u64* pend, int k, int lane) {
+                               u64* pend, int k, int lane, uint32_t ibase) {
     const u64 mx = (1ull << g.bx) - 1ull, my = (1ull << g.by) - 1ull;
     for (int64_t ub = 0; ub < g.ncells; ub += 32) {
         const int64_t u = ub + lane;
@@ -222,37 +225,65 @@ __device__ void scan_all_cells(const Grid& g, float qx, float qy, float qz, Sear
                 cnt = g.cell_start[u + 1] - start;
             }
         }
-        scan_ranges(g, qx, qy, qz, start, cnt, INFINITY, S, pend, k, lane);
+        scan_ranges(g, qx, qy, qz, start, cnt, INFINITY, S, pend, k, lane, ibase);
     }
+}
+
+// The cell box of radius rho around q on one grid, clamped to its window
+// range (the whole grid when no window is set), and the certified tau of
+// the unclamped box.
+struct WarpBox {
+    int lx, ly, lz;
+    int ex, ey, ez;
+    int64_t ncl;
+    float tau;
+};
+
+__device__ __forceinline__ WarpBox warp_box(const Grid& g, float qx, float qy, float qz, float rho) {
+    const int lx = cell_of(__fsub_rn(qx, rho), g.ox, g.inv_h);
+    const int hx = cell_of(__fadd_rn(qx, rho), g.ox, g.inv_h);
+    const int ly = cell_of(__fsub_rn(qy, rho), g.oy, g.inv_h);
+    const int hy = cell_of(__fadd_rn(qy, rho), g.oy, g.inv_h);
+    const int lz = cell_of(__fsub_rn(qz, rho), g.oz, g.inv_h);
+    const int hz = cell_of(__fadd_rn(qz, rho), g.oz, g.inv_h);
+    WarpBox b;
+    b.tau = certified_tau(g, qx, qy, qz, lx, hx, ly, hy, lz, hz);
+    b.lx = max(lx, g.wlx);
+    b.ly = max(ly, g.wly);
+    b.lz = max(lz, g.wlz);
+    b.ex = max(min(hx, g.whx) - b.lx + 1, 0);
+    b.ey = max(min(hy, g.why) - b.ly + 1, 0);
+    b.ez = max(min(hz, g.whz) - b.lz + 1, 0);
+    b.ncl = (int64_t)b.ex * b.ey * b.ez;
+    return b;
 }
 
 // Exact k nearest neighbours of one query (warp-uniform control flow).
 // Returns SEARCH_OK, SEARCH_LIMIT (max_box_cells reached with exhaustive =
 // 0) or SEARCH_SHORT (the exhaustive scan found fewer than k points: the
-// window holds fewer than k).
+// window holds fewer than k).  With DEL the search runs over the union of
+// g and the appended-points grid dg, whose point j is g.m + j: every
+// attempt scans both grids' boxes of the same radius, filtered by the
+// smaller of their two certified taus (a point of either grid outside its
+// box lies beyond both), and the exhaustive scan covers both grids.
 constexpr int SEARCH_OK = 0, SEARCH_LIMIT = 1, SEARCH_SHORT = 2;
-template <int SLOTS>
-__device__ int knn_search(const Grid& g, float qx, float qy, float qz, int k, float& rho,
-                           SearchState<SLOTS>& S, u64* pend, int lane) {
+template <int SLOTS, bool DEL>
+__device__ int knn_search(const Grid& g, const Grid& dg, float qx, float qy, float qz, int k, float& rho,
+                          SearchState<SLOTS>& S, u64* pend, int lane) {
     for (int attempt = 0; attempt < 40; ++attempt) {
-        const int lx = cell_of(__fsub_rn(qx, rho), g.ox, g.inv_h);
-        const int hx = cell_of(__fadd_rn(qx, rho), g.ox, g.inv_h);
-        const int ly = cell_of(__fsub_rn(qy, rho), g.oy, g.inv_h);
-        const int hy = cell_of(__fadd_rn(qy, rho), g.oy, g.inv_h);
-        const int lz = cell_of(__fsub_rn(qz, rho), g.oz, g.inv_h);
-        const int hz = cell_of(__fadd_rn(qz, rho), g.oz, g.inv_h);
-        const float tau = certified_tau(g, qx, qy, qz, lx, hx, ly, hy, lz, hz);
-        const int cxl = max(lx, g.wlx), cxh = min(hx, g.whx);
-        const int cyl = max(ly, g.wly), cyh = min(hy, g.why);
-        const int czl = max(lz, g.wlz), czh = min(hz, g.whz);
-        const int64_t ex = max(cxh - cxl + 1, 0), ey = max(cyh - cyl + 1, 0),
-                      ez = max(czh - czl + 1, 0);
-        const int64_t ncl = ex * ey * ez;
-        if (ncl > (int64_t)g.max_box_cells) break;
+        const WarpBox b = warp_box(g, qx, qy, qz, rho);
+        WarpBox d = b;
+        float tau = b.tau;
+        if (DEL) {
+            d = warp_box(dg, qx, qy, qz, rho);
+            tau = fminf(tau, d.tau);
+            if (d.ncl > (int64_t)dg.max_box_cells) break;
+        }
+        if (b.ncl > (int64_t)g.max_box_cells) break;
         state_reset(S);
-        if (ncl > 0)
-            scan_box(g, qx, qy, qz, cxl, cyl, czl, (int)ex, (int)ey, (int)ez, tau, S, pend, k,
-                     lane);
+        if (b.ncl > 0) scan_box(g, qx, qy, qz, b.lx, b.ly, b.lz, b.ex, b.ey, b.ez, tau, S, pend, k, lane, 0u);
+        if (DEL && d.ncl > 0)
+            scan_box(dg, qx, qy, qz, d.lx, d.ly, d.lz, d.ex, d.ey, d.ez, tau, S, pend, k, lane, (uint32_t)g.m);
         flush(S, pend, k, lane);
         if (S.kth != EMPTY_KEY) return SEARCH_OK;
         int found = 0;
@@ -265,7 +296,8 @@ __device__ int knn_search(const Grid& g, float qx, float qy, float qz, int k, fl
     if (!g.exhaustive) return SEARCH_LIMIT;
     if (lane == 0) atomicAdd(&g.stats[2], 1ull);
     state_reset(S);
-    scan_all_cells(g, qx, qy, qz, S, pend, k, lane);
+    scan_all_cells(g, qx, qy, qz, S, pend, k, lane, 0u);
+    if (DEL) scan_all_cells(dg, qx, qy, qz, S, pend, k, lane, (uint32_t)g.m);
     flush(S, pend, k, lane);
     return S.kth != EMPTY_KEY ? SEARCH_OK : SEARCH_SHORT;
 }
@@ -415,6 +447,42 @@ __device__ void cov_row(const Grid& g, const int32_t* nb, int st, int k, float e
     cov_core([&](int j) { return __ldg(&g.xyz[nb[j * st]]); }, k, eps, out);
 }
 
+// Positions in the lane lists: a main-grid position, or an appended-points
+// grid position with DTAG set (both grids hold fewer than 2^31 points).
+constexpr uint32_t DTAG = 0x80000000u;
+
+template <bool DEL>
+__device__ __forceinline__ float4 pt_at(const Grid& g, const Grid& dg, uint32_t tp) {
+    if (!DEL) return __ldg(&g.pts[tp]);
+    const float4* base = (tp & DTAG) ? dg.pts : g.pts;
+    return __ldg(&base[tp & ~DTAG]);
+}
+
+// Index of the point at tagged position tp in the union numbering: main
+// points keep their index, appended point j is g.m + j.
+template <bool DEL>
+__device__ __forceinline__ uint32_t union_index(const Grid& g, uint32_t tp, float4 p) {
+    const uint32_t i = __float_as_uint(p.w);
+    return (DEL && (tp & DTAG)) ? (uint32_t)g.m + i : i;
+}
+
+// cov_row over the union numbering (a leading -1 marks an unanswered row).
+template <bool DEL>
+__device__ void cov_row_union(const Grid& g, const Grid& dg, const int32_t* nb, int k, float eps, float* out) {
+    if (!DEL) {
+        cov_row(g, nb, 1, k, eps, out, false);
+        return;
+    }
+    if (nb[0] < 0) {
+        nan_row(out);
+        return;
+    }
+    cov_core([&](int j) {
+        const int64_t i = nb[j];
+        return i < g.m ? __ldg(&g.xyz[i]) : __ldg(&dg.xyz[i - g.m]);
+    }, k, eps, out);
+}
+
 // ---------------------------------------------------------------- tiles
 struct TileArgs {
     int k;
@@ -467,11 +535,13 @@ __device__ __forceinline__ float rad_mul(int j) {
 }
 
 // (d2, index) key of the survivor in a lane's slot, recomputed from pts.
-__device__ __forceinline__ u64 slot_key(const Grid& g, const uint32_t* posl, int slot, int lane,
-                                        float qx, float qy, float qz) {
-    const float4 p = __ldg(&g.pts[posl[slot * 32 + lane]]);
+template <bool DEL>
+__device__ __forceinline__ u64 slot_key(const Grid& g, const Grid& dg, const uint32_t* posl, int slot,
+                                        int lane, float qx, float qy, float qz) {
+    const uint32_t tp = posl[slot * 32 + lane];
+    const float4 p = pt_at<DEL>(g, dg, tp);
     const float d = sqdist_pinned(qx, qy, qz, p.x, p.y, p.z);
-    return ((u64)__float_as_uint(d) << 32) | (u64)__float_as_uint(p.w);
+    return ((u64)__float_as_uint(d) << 32) | (u64)union_index<DEL>(g, tp, p);
 }
 
 // k <= 32: one query per lane.  Pass 1 counts, for each trial radius
@@ -487,8 +557,13 @@ __device__ __forceinline__ u64 slot_key(const Grid& g, const uint32_t* posl, int
 // index) order by bubble passes on the full keys.  Lanes whose query needs
 // a wider radius, more than 32 survivors or a bigger box are finished by
 // the warp-cooperative search, one query at a time.
-template <int CAP, bool COV, bool WIN>
-__device__ void lane_tile(const Grid& g, const float* __restrict__ q, int64_t n0, int cnt,
+//
+// With DEL the search covers the union of the main grid g and the grid dg of
+// appended points (point j of dg is g.m + j): both grids' boxes of the trial
+// radius are counted and collected in the same passes, filtered by the
+// smaller of their certified taus, and list entries from dg carry DTAG.
+template <int CAP, bool COV, bool WIN, bool DEL>
+__device__ void lane_tile(const Grid& g, const Grid& dg, const float* __restrict__ q, int64_t n0, int cnt,
                           const TileArgs& a, float rho0, int32_t* __restrict__ idx,
                           float* __restrict__ d2, float* __restrict__ cov, u64* pend,
                           uint32_t* posl, int lane) {
@@ -507,6 +582,8 @@ __device__ void lane_tile(const Grid& g, const float* __restrict__ q, int64_t n0
     float thr = -1.0f;
     int lx = 0, hx = -1, ly = 0, hy = -1, lz = 0, hz = -1;
     float eta = 0.0f;
+    int dlx = 0, dhx = -1, dly = 0, dhy = -1, dlz = 0, dhz = -1;
+    float deta = 0.0f;
     // Up to two lane-parallel attempts: a lane whose largest trial radius
     // held fewer than k points retries with the radii x1.8, one whose
     // smallest held more than CAP retries with them x0.7; only lanes that
@@ -523,11 +600,11 @@ __device__ void lane_tile(const Grid& g, const float* __restrict__ q, int64_t n0
             const int uhy = cell_of(__fadd_rn(qy, rmax), g.oy, g.inv_h);
             const int ulz = cell_of(__fsub_rn(qz, rmax), g.oz, g.inv_h);
             const int uhz = cell_of(__fadd_rn(qz, rmax), g.oz, g.inv_h);
-            const float tau = certified_tau(g, qx, qy, qz, ulx, uhx, uly, uhy, ulz, uhz);
+            float tau = certified_tau(g, qx, qy, qz, ulx, uhx, uly, uhy, ulz, uhz);
+            const float qm = fmaxf(fabsf(qx), fmaxf(fabsf(qy), fabsf(qz)));
             {
                 const int cm = max(max(max(abs(ulx), abs(uhx + 1)), max(abs(uly), abs(uhy + 1))),
                                    max(abs(ulz), abs(uhz + 1)));
-                const float qm = fmaxf(fabsf(qx), fmaxf(fabsf(qy), fabsf(qz)));
                 eta = 0x1p-20f * (g.coord_scale + qm + (float)cm * g.h);
             }
             lx = max(ulx, WIN ? g.wlx : 0); hx = min(uhx, WIN ? g.whx : g.dimx - 1);
@@ -535,8 +612,28 @@ __device__ void lane_tile(const Grid& g, const float* __restrict__ q, int64_t n0
             lz = max(ulz, WIN ? g.wlz : 0); hz = min(uhz, WIN ? g.whz : g.dimz - 1);
             const int64_t ncl = (int64_t)max(hx - lx + 1, 0) * max(hy - ly + 1, 0) * max(hz - lz + 1, 0);
             const int64_t nrows = (int64_t)max(hy - ly + 1, 0) * max(hz - lz + 1, 0);
+            bool big = ncl > 4096 || nrows > 256 || (!g.occ && ncl > 256);
+            if (DEL) {
+                const int vlx = cell_of(__fsub_rn(qx, rmax), dg.ox, dg.inv_h);
+                const int vhx = cell_of(__fadd_rn(qx, rmax), dg.ox, dg.inv_h);
+                const int vly = cell_of(__fsub_rn(qy, rmax), dg.oy, dg.inv_h);
+                const int vhy = cell_of(__fadd_rn(qy, rmax), dg.oy, dg.inv_h);
+                const int vlz = cell_of(__fsub_rn(qz, rmax), dg.oz, dg.inv_h);
+                const int vhz = cell_of(__fadd_rn(qz, rmax), dg.oz, dg.inv_h);
+                tau = fminf(tau, certified_tau(dg, qx, qy, qz, vlx, vhx, vly, vhy, vlz, vhz));
+                const int cm = max(max(max(abs(vlx), abs(vhx + 1)), max(abs(vly), abs(vhy + 1))),
+                                   max(abs(vlz), abs(vhz + 1)));
+                deta = 0x1p-20f * (dg.coord_scale + qm + (float)cm * dg.h);
+                dlx = max(vlx, WIN ? dg.wlx : 0); dhx = min(vhx, WIN ? dg.whx : dg.dimx - 1);
+                dly = max(vly, WIN ? dg.wly : 0); dhy = min(vhy, WIN ? dg.why : dg.dimy - 1);
+                dlz = max(vlz, WIN ? dg.wlz : 0); dhz = min(vhz, WIN ? dg.whz : dg.dimz - 1);
+                const int64_t dncl =
+                    (int64_t)max(dhx - dlx + 1, 0) * max(dhy - dly + 1, 0) * max(dhz - dlz + 1, 0);
+                const int64_t dnrows = (int64_t)max(dhy - dly + 1, 0) * max(dhz - dlz + 1, 0);
+                big = big || dncl > 4096 || dnrows > 256 || (!dg.occ && dncl > 256);
+            }
             fallback = false;
-            if (tau < 0.0f || ncl > 4096 || nrows > 256 || (!g.occ && ncl > 256)) {
+            if (tau < 0.0f || big) {
                 fallback = true;
             } else {
                 float t[NRAD];
@@ -554,6 +651,13 @@ __device__ void lane_tile(const Grid& g, const float* __restrict__ q, int64_t n0
                 };
                 if (g.occ) for_rows<WIN>(g, qx, qy, qz, lx, hx, ly, hy, lz, hz, eta, t[NRAD - 1], count);
                 else for_box_points<WIN>(g, qx, qy, qz, lx, hx, ly, hy, lz, hz, eta, t[NRAD - 1], count);
+                if (DEL) {
+                    if (dg.occ)
+                        for_rows<WIN>(dg, qx, qy, qz, dlx, dhx, dly, dhy, dlz, dhz, deta, t[NRAD - 1], count);
+                    else
+                        for_box_points<WIN>(dg, qx, qy, qz, dlx, dhx, dly, dhy, dlz, dhz, deta, t[NRAD - 1],
+                                            count);
+                }
                 int js = -1;
 #pragma unroll
                 for (int j = NRAD - 1; j >= 0; --j)
@@ -590,6 +694,11 @@ __device__ void lane_tile(const Grid& g, const float* __restrict__ q, int64_t n0
         };
         if (g.occ) for_rows<WIN>(g, qx, qy, qz, lx, hx, ly, hy, lz, hz, eta, thr, collect);
         else for_box_points<WIN>(g, qx, qy, qz, lx, hx, ly, hy, lz, hz, eta, thr, collect);
+        if (DEL) {
+            auto collect_d = [&](uint32_t pos, const float4 p) { collect(pos | DTAG, p); };
+            if (dg.occ) for_rows<WIN>(dg, qx, qy, qz, dlx, dhx, dly, dhy, dlz, dhz, deta, thr, collect_d);
+            else for_box_points<WIN>(dg, qx, qy, qz, dlx, dhx, dly, dhy, dlz, dhz, deta, thr, collect_d);
+        }
     }
     __syncwarp();
     uint32_t K[CAP];
@@ -597,7 +706,7 @@ __device__ void lane_tile(const Grid& g, const float* __restrict__ q, int64_t n0
     for (int s = 0; s < CAP; ++s) {
         uint32_t key = 0xffffffffu;
         if (s < m) {
-            const float4 p = __ldg(&g.pts[posl[s * 32 + lane]]);
+            const float4 p = pt_at<DEL>(g, dg, posl[s * 32 + lane]);
             const float d = sqdist_pinned(qx, qy, qz, p.x, p.y, p.z);
             key = ((__float_as_uint(d) << 1) & ~(uint32_t)(CAP - 1)) | (uint32_t)s;
         }
@@ -615,8 +724,8 @@ __device__ void lane_tile(const Grid& g, const float* __restrict__ q, int64_t n0
 #pragma unroll
         for (int r = 0; r + 1 < CAP; ++r) {
             if (r + 1 < m && ((K[r] ^ K[r + 1]) < (uint32_t)CAP)) {
-                const u64 ka = slot_key(g, posl, (int)(K[r] & (CAP - 1)), lane, qx, qy, qz);
-                const u64 kb = slot_key(g, posl, (int)(K[r + 1] & (CAP - 1)), lane, qx, qy, qz);
+                const u64 ka = slot_key<DEL>(g, dg, posl, (int)(K[r] & (CAP - 1)), lane, qx, qy, qz);
+                const u64 kb = slot_key<DEL>(g, dg, posl, (int)(K[r + 1] & (CAP - 1)), lane, qx, qy, qz);
                 if (kb < ka) {
                     const uint32_t tmp = K[r];
                     K[r] = K[r + 1];
@@ -640,8 +749,8 @@ __device__ void lane_tile(const Grid& g, const float* __restrict__ q, int64_t n0
         const int vw = ((k & 3) == 0 && (ab & 15) == 0) ? 4 : (((k & 1) == 0 && (ab & 7) == 0) ? 2 : 1);
         auto entry = [&](int r, int& iv, float& dv) {
             posl[r * 32 + lane] = P[r];
-            const float4 p = __ldg(&g.pts[P[r]]);
-            iv = (int)__float_as_uint(p.w);
+            const float4 p = pt_at<DEL>(g, dg, P[r]);
+            iv = (int)union_index<DEL>(g, P[r], p);
             dv = sqdist_pinned(qx, qy, qz, p.x, p.y, p.z);
         };
         if (vw == 4) {
@@ -699,7 +808,7 @@ __device__ void lane_tile(const Grid& g, const float* __restrict__ q, int64_t n0
         float rho = rho0 * rad_mul(NRAD - 1);
         SearchState<1> S;
         state_reset(S);
-        const int sr = knn_search<1>(g, fx, fy, fz, k, rho, S, pend, lane);
+        const int sr = knn_search<1, DEL>(g, dg, fx, fy, fz, k, rho, S, pend, lane);
         const bool ok = sr == SEARCH_OK;
         if (!ok && lane == 0) atomicOr(g.status, sr == SEARCH_SHORT ? ST_SHORT : ST_SEARCH_LIMIT);
         const int64_t nf = n0 + f;
@@ -711,16 +820,16 @@ __device__ void lane_tile(const Grid& g, const float* __restrict__ q, int64_t n0
     if (COV && cov != nullptr) {
         __syncwarp();  // orders the idx rows written by other lanes
         if (m > 0)  // neighbours straight from the cell-sorted copy, in rank order
-            cov_core([&](int j) { return __ldg(&g.pts[posl[j * 32 + lane]]); }, k, a.eps, cov + 6 * n);
+            cov_core([&](int j) { return pt_at<DEL>(g, dg, posl[j * 32 + lane]); }, k, a.eps, cov + 6 * n);
         else if (active)
-            cov_row(g, idx + n * k, 1, k, a.eps, cov + 6 * n, false);
+            cov_row_union<DEL>(g, dg, idx + n * k, k, a.eps, cov + 6 * n);
     }
     __syncwarp();
 }
 
 // k > 32: the warp-cooperative search for each query of the tile in turn.
-template <bool COV>
-__device__ void warp_tile(const Grid& g, const float* __restrict__ q, int64_t n0, int cnt,
+template <bool COV, bool DEL>
+__device__ void warp_tile(const Grid& g, const Grid& dg, const float* __restrict__ q, int64_t n0, int cnt,
                           const TileArgs& a, float rho0, int32_t* __restrict__ idx,
                           float* __restrict__ d2, float* __restrict__ cov, u64* pend,
                           int lane) {
@@ -737,7 +846,7 @@ __device__ void warp_tile(const Grid& g, const float* __restrict__ q, int64_t n0
         SearchState<2> S;
         state_reset(S);
         int sr = SEARCH_LIMIT;
-        if (finite) sr = knn_search<2>(g, qx, qy, qz, k, rho, S, pend, lane);
+        if (finite) sr = knn_search<2, DEL>(g, dg, qx, qy, qz, k, rho, S, pend, lane);
         const bool ok = finite && sr == SEARCH_OK;
         if (!ok && lane == 0)
             atomicOr(g.status, !finite ? ST_NONFINITE : sr == SEARCH_SHORT ? ST_SHORT : ST_SEARCH_LIMIT);
@@ -758,13 +867,13 @@ __device__ void warp_tile(const Grid& g, const float* __restrict__ q, int64_t n0
     }
     if (COV && cov != nullptr) {
         __syncwarp();
-        if (lane < cnt) cov_row(g, idx + (n0 + lane) * k, 1, k, a.eps, cov + 6 * (n0 + lane), false);
+        if (lane < cnt) cov_row_union<DEL>(g, dg, idx + (n0 + lane) * k, k, a.eps, cov + 6 * (n0 + lane));
         __syncwarp();
     }
 }
 
-template <int MODE, bool COV, bool WIN>
-__device__ __forceinline__ void process_tile(const Grid& g, const float* __restrict__ q, int64_t n0,
+template <int MODE, bool COV, bool WIN, bool DEL = false>
+__device__ __forceinline__ void process_tile(const Grid& g, const Grid& dg, const float* __restrict__ q, int64_t n0,
                                              int cnt, const TileArgs& a, float rho0,
                                              int32_t* __restrict__ idx, float* __restrict__ d2,
                                              float* __restrict__ cov, unsigned char* wsmem,
@@ -772,11 +881,11 @@ __device__ __forceinline__ void process_tile(const Grid& g, const float* __restr
     u64* pend = reinterpret_cast<u64*>(wsmem);
     uint32_t* posl = reinterpret_cast<uint32_t*>(wsmem + 64 * sizeof(u64));
     if (MODE == 0)
-        lane_tile<32, COV, WIN>(g, q, n0, cnt, a, rho0, idx, d2, cov, pend, posl, lane);
+        lane_tile<32, COV, WIN, DEL>(g, dg, q, n0, cnt, a, rho0, idx, d2, cov, pend, posl, lane);
     else if (MODE == 1)
-        lane_tile<64, COV, WIN>(g, q, n0, cnt, a, rho0, idx, d2, cov, pend, posl, lane);
+        lane_tile<64, COV, WIN, DEL>(g, dg, q, n0, cnt, a, rho0, idx, d2, cov, pend, posl, lane);
     else
-        warp_tile<COV>(g, q, n0, cnt, a, rho0, idx, d2, cov, pend, lane);
+        warp_tile<COV, DEL>(g, dg, q, n0, cnt, a, rho0, idx, d2, cov, pend, lane);
 }
 
 template <int MODE, bool COV, bool WIN>
@@ -797,8 +906,8 @@ __global__ void __launch_bounds__(256, 2) k_knn(Grid g, const float* __restrict_
     const int64_t t = a.last_first ? tiles - 1 - w : w;
     const int64_t n0 = t * tile;
     const int cnt = (int)min((int64_t)tile, N - n0);
-    process_tile<MODE, COV, WIN>(g, q, n0, cnt, a, rho0, idx, d2, cov,
-                            smem + (size_t)warp * warp_smem_bytes(MODE), lane);
+    process_tile<MODE, COV, WIN>(g, g, q, n0, cnt, a, rho0, idx, d2, cov,
+                                 smem + (size_t)warp * warp_smem_bytes(MODE), lane);
 }
 
 // Batched form: one persistent launch; warps pull (scan, tile) items from a
@@ -824,8 +933,29 @@ __global__ void __launch_bounds__(256, 2) k_knn_batch(Grid g, const ScanDesc* __
         const ScanDesc sd = scans[lo];
         const int64_t n0 = ((int64_t)item - sd.tile0) * tile;
         const int cnt = (int)min((int64_t)tile, sd.n - n0);
-        process_tile<MODE, COV, WIN>(g, sd.q, n0, cnt, a, rho0, sd.idx, sd.d2, sd.cov, wsmem, lane);
+        process_tile<MODE, COV, WIN>(g, g, sd.q, n0, cnt, a, rho0, sd.idx, sd.d2, sd.cov, wsmem, lane);
     }
+}
+
+// Search over a map grown by appended points: the main grid g and the
+// appended-points grid dg as one map (indices of dg's points follow g's).
+// Same tiling and tile order as k_knn.
+template <int MODE, bool COV, bool WIN>
+__global__ void __launch_bounds__(256, 2) k_knn_union(Grid g, Grid dg, const float* __restrict__ q, int64_t N,
+                                                   int tile, TileArgs a, float rho0,
+                                                   int32_t* __restrict__ idx, float* __restrict__ d2,
+                                                   float* __restrict__ cov) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nwarps = blockDim.x >> 5;
+    const int64_t tiles = (N + tile - 1) / tile;
+    const int64_t w = (int64_t)blockIdx.x * nwarps + warp;
+    if (w >= tiles) return;
+    const int64_t t = a.last_first ? tiles - 1 - w : w;
+    const int64_t n0 = t * tile;
+    const int cnt = (int)min((int64_t)tile, N - n0);
+    process_tile<MODE, COV, WIN, true>(g, dg, q, n0, cnt, a, rho0, idx, d2, cov,
+                                       smem + (size_t)warp * warp_smem_bytes(MODE), lane);
 }
 
 __global__ void k_cov(Grid g, const int32_t* __restrict__ idx, int64_t N, int k, float eps,
@@ -853,6 +983,28 @@ void* knn_kernel(int mode, bool with_cov, bool batch) {
         default: return PC_PICK(2, true);
     }
 #undef PC_PICK
+}
+
+// The union search kernel for (mode, covariance) of this window variant.
+template <bool WIN>
+void* knn_union_kernel(int mode, bool with_cov) {
+    switch (mode * 2 + (with_cov ? 1 : 0)) {
+        case 0: return (void*)k_knn_union<0, false, WIN>;
+        case 1: return (void*)k_knn_union<0, true, WIN>;
+        case 2: return (void*)k_knn_union<1, false, WIN>;
+        case 3: return (void*)k_knn_union<1, true, WIN>;
+        case 4: return (void*)k_knn_union<2, false, WIN>;
+        default: return (void*)k_knn_union<2, true, WIN>;
+    }
+}
+
+template <bool WIN>
+cudaError_t allow_union_smem() {
+    cudaError_t e = cudaSuccess;
+    for (int mode = 0; mode < 3; ++mode)
+        for (int c = 0; c < 2; ++c)
+            if ((e = allow_smem(knn_union_kernel<WIN>(mode, c != 0))) != cudaSuccess) return e;
+    return cudaSuccess;
 }
 
 // Opts every search kernel of this window variant into large dynamic

@@ -172,28 +172,12 @@ static pc_status build_target_internal(const float* xyz, int64_t M, const pc_bui
     return PC_OK;
 }
 
-static pc_status ensure_stage2(pc_target_s* t, size_t bytes) {
-    if (t->stage2_bytes >= bytes) return PC_OK;
-    if (t->stage2) cudaFree(t->stage2);
-    t->stage2 = nullptr;
-    t->stage2_bytes = 0;
-    void* p = nullptr;
-    cudaError_t e = cudaMalloc(&p, bytes);
-    if (e != cudaSuccess) return pc_from_cuda(e);
-    t->stage2 = p;
-    t->stage2_bytes = bytes;
-    return PC_OK;
-}
-
 // The search over the target as it stands: its grid, or its grid and the
-// delta grid of appended points merged.
+// delta grid of appended points searched as one map.
 static pc_status launch_search(pc_target_s* t, const float* q, int64_t N, int k, float eps, int32_t* idx,
                                float* d2, float* cov, cudaStream_t st) {
     if (!t->delta) return pc_from_cuda(pc_launch_knn(t, q, N, k, eps, idx, d2, cov, pc_rho0(t, k), st));
-    const size_t need = pc_union_temp_bytes(t, N, k);
-    pc_status r = need ? ensure_stage2(t, need) : PC_OK;
-    if (r != PC_OK) return r;
-    return pc_from_cuda(pc_launch_knn_union(t, q, N, k, eps, idx, d2, cov, t->stage2, st));
+    return pc_from_cuda(pc_launch_knn_union(t, q, N, k, eps, idx, d2, cov, pc_rho0(t, k), st));
 }
 
 static void free_delta(pc_target_s* t) {
@@ -261,8 +245,6 @@ void pc_destroy_target(pc_target t) {
     untrack(t);
     DeviceGuard dg(t->device);
     free_delta(t);
-    if (t->stage2) cudaFree(t->stage2);
-    t->stage2 = nullptr;
     pc_free_grid(t);
     t->magic = PC_MAGIC_DEAD;
     delete t;
@@ -300,7 +282,7 @@ pc_status pc_get_info(pc_target t, pc_target_info* info) {
     info->dims[0] = t->g.dimx;
     info->dims[1] = t->g.dimy;
     info->dims[2] = t->g.dimz;
-    info->device_bytes = t->device_bytes + (int64_t)t->stage_bytes + (int64_t)t->stage2_bytes +
+    info->device_bytes = t->device_bytes + (int64_t)t->stage_bytes +
                          (t->delta ? t->delta->device_bytes : 0) + (int64_t)sizeof(float) * 3 * t->delta_cap;
     for (int i = 0; i < 64; ++i) info->rho_hint[i] = t->rho_hint[i];
     info->delta_m = t->delta_m;

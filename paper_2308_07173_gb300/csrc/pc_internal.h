@@ -63,9 +63,6 @@ struct pc_target_s {
     // the window of pc_set_window, kept to re-apply to a rebuilt delta grid
     pc_window win;
     int has_win;
-    // staging for the merge of main and delta searches, grown on demand
-    void* stage2;
-    size_t stage2_bytes;
 };
 
 struct pc_batch_s {
@@ -122,6 +119,8 @@ cudaError_t pc_knn_win_attrs();
 // knn_cov.cu
 cudaError_t pc_launch_knn(const pc_target_s* t, const float* q, int64_t N, int k, float eps,
                           int32_t* idx, float* d2, float* cov, float rho0, cudaStream_t s);
+cudaError_t pc_launch_knn_union(const pc_target_s* t, const float* q, int64_t N, int k, float eps,
+                                int32_t* idx, float* d2, float* cov, float rho0, cudaStream_t s);
 cudaError_t pc_launch_cov(const pc_target_s* t, const int32_t* idx, int64_t N, int k, float eps,
                           float* cov, cudaStream_t s);
 cudaError_t pc_launch_knn_batch(const pc_target_s* t, const pcdev::Grid& g, const CovKernel& ck,
@@ -140,12 +139,18 @@ cudaError_t pc_launch_gicp_linearize(const pc_target_s* t, const float* map_cov,
 cudaError_t pc_launch_gicp_update(const double* lin, float lambda, float* pose, double* xi,
                                   cudaStream_t s);
 
-// delta.cu: searches over the main grid plus the delta grid
-cudaError_t pc_launch_knn_union(const pc_target_s* t, const float* q, int64_t N, int k, float eps,
-                                int32_t* idx, float* d2, float* cov, void* temp, cudaStream_t s);
-size_t pc_union_temp_bytes(const pc_target_s* t, int64_t N, int k);
+// knn_union.cu / knn_union_win.cu: the search kernels over the main grid
+// plus the delta grid (whole-map and window variants)
+void* pc_knn_union_kernel(int mode, bool with_cov);
+cudaError_t pc_knn_union_attrs();
+void* pc_knn_union_kernel_win(int mode, bool with_cov);
+cudaError_t pc_knn_union_win_attrs();
+
+// delta.cu: covariances and packing over the main grid plus the delta grid
 cudaError_t pc_launch_cov_union(const pc_target_s* t, const int32_t* idx, int64_t N, int k, float eps,
                                 float* cov, cudaStream_t s);
+cudaError_t pc_launch_cov_weighted_union(const pc_target_s* t, const float* q, const int32_t* idx, int64_t N,
+                                         int k, float eps, float* cov, cudaStream_t s);
 cudaError_t pc_launch_pack_xyz(const pc_target_s* t, float* out, cudaStream_t s);
 
 // cov_weighted.cu

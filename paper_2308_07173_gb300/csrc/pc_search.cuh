@@ -103,11 +103,14 @@ __device__ __forceinline__ uint2 row_part(const Grid& g, float qx, float qy, flo
 
 // Same visit as for_box_points through the row index: every row of the box
 // is one contiguous range of pts.  Rows are resolved two at a time so their
-// index loads overlap.
+// index loads overlap.  An empty box (a query beyond the grid or the window
+// on some axis) visits nothing: the row walk below assumes ly <= hy, and a
+// row index outside [0, dimy) would address the wrong row of the bitmap.
 template <bool WIN = true, typename F>
 __device__ __forceinline__ void for_rows(const Grid& g, float qx, float qy, float qz, int lx, int hx,
                                          int ly, int hy, int lz, int hz, float eta, float tmax,
                                          F&& f) {
+    if (lx > hx || ly > hy) return;
     const float tx = tmax * (1.0f + 0x1p-18f);
     // the window's boundary cells along x are in every row of the box
     const bool wx = WIN && g.windowed && (lx == g.tlx || hx == g.thx);

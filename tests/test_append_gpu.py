@@ -74,6 +74,23 @@ def test_append_equals_oracle_over_the_union(scene, gpu_lib):
     t.close()
 
 
+@pytest.mark.parametrize("k", [10, 32, 40])
+def test_union_search_modes_with_fused_covariance(scene, gpu_lib, k):
+    # k = 10 and 32 run the lane path over both grids (32 and 64 survivor
+    # slots), k = 40 the warp search; the regularised covariance is fused
+    s = scene
+    t = grown_target(gpu_lib, s["map"], 240_000, [60_000])
+    idx, d2, cov = (host(x) for x in t.knn_cov(dev(s["q"]), k, 1e-3))
+    assert t.sync_status() == gpu_lib.PC_OK
+    want_i, want_d = s["tree"].knn(s["q"], k)
+    np.testing.assert_array_equal(idx, want_i)
+    np.testing.assert_array_equal(d2.view(np.uint32), want_d.view(np.uint32))
+    assert (idx >= 240_000).any()
+    raw = host(t.cov(dev(idx), -1.0))
+    H.check_regularised_cov(cov, oracle.cov(s["map"], idx, 1e-3), oracle.cov(s["map"], idx, -1.0), raw, 1e-3)
+    t.close()
+
+
 def test_k_larger_than_the_main_grid(gpu_lib):
     g = np.random.default_rng(3)
     mp = (g.random((60, 3)) * 4).astype(np.float32)
