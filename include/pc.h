@@ -267,15 +267,16 @@ PC_API pc_status pc_get_stats(pc_target t, pc_stream s, pc_stats *out, int reset
  * last call, or PC_ERR_CUDA if the stream reported an error. */
 PC_API pc_status pc_sync_status(pc_target t, pc_stream s);
 
-/* Batched form: many scans against one target in ONE persistent launch that
- * pulls (scan, tile) work items from a device counter, replayed as a CUDA
- * graph.  pc_batch_plan copies the scan table to the device; the pointers in
- * `scans` must stay valid while the plan is used.  All scans share k and eps.
- * Results are bit-identical to pc_knn_cov on each scan alone. */
+/* Batched form: many scans against one target in ONE launch, one warp per
+ * (scan, tile) item of the scans' prefix-summed tile table, replayed as a
+ * CUDA graph.  pc_batch_plan copies the scan table to the device; the
+ * pointers in `scans` must stay valid while the plan is used.  All scans
+ * share k and eps.  Results are bit-identical to pc_knn_cov on each scan
+ * alone. */
 PC_API pc_status pc_batch_plan(pc_target t, const pc_scan *scans, int n_scans, int k, float eps,
                         pc_batch *out);
-/* Runs the plan on `s`.  The first run on a stream captures a CUDA graph
- * (counter reset + persistent kernel); later runs replay it. */
+/* Runs the plan on `s`.  The first run on a stream captures the launch in a
+ * CUDA graph; later runs replay it. */
 PC_API pc_status pc_batch_run(pc_batch b, pc_stream s);
 PC_API void pc_batch_destroy(pc_batch b);
 
@@ -285,7 +286,7 @@ PC_API size_t pc_batch_scratch_bytes(int n_scans);
 /* The batched form (same kernel and results as pc_batch_run) with scratch
  * the caller owns: scratch_dev is device memory of at least
  * pc_batch_scratch_bytes(n_scans) bytes, 256-byte aligned, used for the scan
- * table and the work counter.  No allocation and no graph.  Calls with
+ * table.  No allocation and no graph.  Calls with
  * distinct scratch may run concurrently on different streams and overlap on
  * the device -- the continuous-batching server launches each step this way.
  * Asynchronous on `s`; the scan table is copied from `scans` before the call
@@ -306,7 +307,7 @@ PC_API pc_status pc_batch_run_scratch(pc_target t, const pc_scan *scans, int n_s
  * device), or an application that hands out every device buffer from its
  * own pool.  It calls no cudaMalloc, cudaFree or other allocating routine.
  *
- * Its scratch -- the scan table and the kernel's work counter -- lives in
+ * Its scratch -- the scan table -- lives in
  * one file-scope device array sized for PC_NOALLOC_MAX_SCANS scans (about
  * 12 KB), which every GPU that loads the library keeps until the process
  * exits.  The caller still passes the target, and the inputs and outputs in
@@ -317,8 +318,7 @@ PC_API pc_status pc_batch_run_scratch(pc_target t, const pc_scan *scans, int n_s
  *    per device, with that device current); make that first call before
  *    any stream capture.
  *  - Every call on a device uses the same array and it keeps the last
- *    call's contents (the counter is cleared at the start of each call):
- *    calls that overlap on the GPU -- on two streams, or from two host
+ *    call's scan table: calls that overlap on the GPU -- on two streams, or from two host
  *    threads -- race and corrupt each other's results.  Serialise them.
  *  - Asynchronous on `s`; the scan table is copied from the caller's host
  *    array before the call returns, so that array may be reused at once.

@@ -124,6 +124,8 @@ cudaError_t pc_launch_knn_union(const pc_target_s* t, const float* q, int64_t N,
     return e;
 }
 
+cudaError_t pc_knn_prepare() { return ensure_attrs(); }
+
 cudaError_t pc_launch_cov(const pc_target_s* t, const int32_t* idx, int64_t N, int k, float eps,
                           float* cov, cudaStream_t s) {
     if (N == 0) return cudaSuccess;
@@ -135,34 +137,24 @@ cudaError_t pc_launch_cov(const pc_target_s* t, const int32_t* idx, int64_t N, i
 
 cudaError_t pc_launch_knn_batch(const pc_target_s* t, const Grid& gv, const CovKernel& ck,
                                 const ScanDesc* scans_dev, int nscans, int64_t max_n,
-                                int64_t total_tiles, int tile, int warps, int blocks, int k,
-                                float eps, bool with_cov, float rho0,
-                                unsigned long long* counter, cudaStream_t s) {
-    TileArgs a{k, eps, t->tune.rho_scale > 0 ? t->tune.rho_scale : 0.9f, 0};
+                                int64_t total_tiles, int tile, int warps, int k, float eps,
+                                bool with_cov, float rho0, cudaStream_t s) {
+    if (total_tiles == 0) return cudaSuccess;
+    cudaError_t e = ensure_attrs();
+    if (e != cudaSuccess) return e;
+    TileArgs a{k, eps, t->tune.rho_scale > 0 ? t->tune.rho_scale : 0.9f, t->tune.order == 0 ? 1 : 0};
+    const int64_t blocks = (total_tiles + warps - 1) / warps;
+    if (blocks > 0x7fffffff) return cudaErrorInvalidValue;
     const int mode = search_mode(k);
     const size_t smem = (size_t)warps * warp_smem_bytes(mode);
     const bool weighted = with_cov && ck.type != 0;
     const bool fused_cov = with_cov && !weighted;
     Grid g = gv;
-    void* args[] = {&g, (void*)&scans_dev, &nscans, &total_tiles, &tile, &a, &rho0, &counter};
-    cudaError_t e = with_kernel<true>(mode, fused_cov, g.windowed != 0, [&](void* kern) {
+    void* args[] = {&g, (void*)&scans_dev, &nscans, &total_tiles, &tile, &a, &rho0};
+    e = with_kernel<true>(mode, fused_cov, g.windowed != 0, [&](void* kern) {
         return cudaLaunchKernel(kern, dim3((unsigned)blocks), dim3(warps * 32), args, smem, s);
     });
     if (e == cudaSuccess && weighted)
         e = pc_launch_cov_weighted_batch(g, ck, scans_dev, nscans, max_n, k, eps, s);
     return e;
-}
-
-int pc_knn_batch_blocks(int k, bool with_cov, int warps) {
-    int dev = 0, sms = 0, per_sm = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (ensure_attrs() != cudaSuccess) return sms;
-    const int mode = search_mode(k);
-    const size_t smem = (size_t)warps * warp_smem_bytes(mode);
-    const cudaError_t e = with_kernel<true>(mode, with_cov, false, [&](void* kern) {
-        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, warps * 32, smem);
-    });
-    if (e != cudaSuccess || per_sm < 1) per_sm = 1;
-    return sms * per_sm;
 }

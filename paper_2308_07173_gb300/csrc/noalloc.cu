@@ -2,8 +2,7 @@
 // device array instead of memory from cudaMalloc, for callers that may not
 // allocate once they are running.  Nothing here allocates: the device
 // address of the array is looked up once per device, the scan table is
-// copied into it, the work counter in it is cleared, and the existing
-// batched launch runs on it.
+// copied into it, and the existing batched launch runs on it.
 #include <cmath>
 #include <mutex>
 
@@ -11,9 +10,7 @@
 
 namespace {
 
-constexpr size_t kCounterOffset = 0;  // u64 work counter
-constexpr size_t kTableOffset = 256;  // ScanDesc[PC_NOALLOC_MAX_SCANS]
-constexpr size_t kScratchBytes = kTableOffset + sizeof(ScanDesc) * PC_NOALLOC_MAX_SCANS;
+constexpr size_t kScratchBytes = sizeof(ScanDesc) * PC_NOALLOC_MAX_SCANS;  // the scan table
 
 // Shared by every call on a device; see the contract in include/pc.h.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
@@ -94,14 +91,11 @@ extern "C" pc_status pc_batch_run_noalloc(pc_target t, const pc_scan* scans, int
     pc_status r = scratch_on_current_device(&scratch);
     if (r != PC_OK) return r;
     cudaStream_t st = (cudaStream_t)s;
-    auto* counter = reinterpret_cast<unsigned long long*>(scratch + kCounterOffset);
-    auto* table_dev = reinterpret_cast<ScanDesc*>(scratch + kTableOffset);
-    const int blocks = pc_knn_batch_blocks(k, any_cov, warps);
+    auto* table_dev = reinterpret_cast<ScanDesc*>(scratch);
     cudaError_t e = cudaMemcpyAsync(table_dev, table, sizeof(ScanDesc) * n_scans,
                                     cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), st);
     if (e == cudaSuccess)
-        e = pc_launch_knn_batch(t, t->g, t->ck, table_dev, n_scans, max_n, tiles, tile, warps, blocks, k, eps, any_cov,
-                                pc_rho0(t, k), counter, st);
+        e = pc_launch_knn_batch(t, t->g, t->ck, table_dev, n_scans, max_n, tiles, tile, warps, k, eps, any_cov,
+                                pc_rho0(t, k), st);
     return pc_from_cuda(e);
 }

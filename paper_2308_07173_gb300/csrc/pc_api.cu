@@ -440,14 +440,12 @@ pc_status pc_batch_plan(pc_target t, const pc_scan* scans, int n_scans, int k, f
     }
     b->total_tiles = tiles;
     b->total_queries = queries;
-    b->blocks = pc_knn_batch_blocks(k, any_cov, b->warps);
-    cudaError_t e = cudaMalloc(&b->scans_dev, sizeof(ScanDesc) * n_scans);
-    if (e == cudaSuccess) e = cudaMalloc(&b->counter, sizeof(unsigned long long));
+    cudaError_t e = pc_knn_prepare();
+    if (e == cudaSuccess) e = cudaMalloc(&b->scans_dev, sizeof(ScanDesc) * n_scans);
     if (e == cudaSuccess)
         e = cudaMemcpy(b->scans_dev, hs.data(), sizeof(ScanDesc) * n_scans, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
         if (b->scans_dev) cudaFree(b->scans_dev);
-        if (b->counter) cudaFree(b->counter);
         delete b;
         return pc_from_cuda(e);
     }
@@ -465,14 +463,10 @@ pc_status pc_batch_run(pc_batch b, pc_stream s) {
     DeviceGuard dg(b->t->device);
     cudaStream_t st = (cudaStream_t)s;
     const float rho0 = pc_rho0(b->t, b->k);
-    if (st == nullptr) {  // the legacy stream cannot be captured: launch directly
-        cudaError_t e = cudaMemsetAsync(b->counter, 0, sizeof(unsigned long long), st);
-        if (e == cudaSuccess)
-            e = pc_launch_knn_batch(b->t, b->g, b->ck, b->scans_dev, b->n_scans, b->max_n, b->total_tiles, b->tile,
-                                    b->warps, b->blocks, b->k, b->eps, b->with_cov, rho0,
-                                    b->counter, st);
-        return pc_from_cuda(e);
-    }
+    if (st == nullptr)  // the legacy stream cannot be captured: launch directly
+        return pc_from_cuda(pc_launch_knn_batch(b->t, b->g, b->ck, b->scans_dev, b->n_scans, b->max_n,
+                                                b->total_tiles, b->tile, b->warps, b->k, b->eps, b->with_cov,
+                                                rho0, st));
     if (!b->exec || b->captured_on != st) {
         if (b->exec) cudaGraphExecDestroy(b->exec);
         if (b->graph) cudaGraphDestroy(b->graph);
@@ -480,12 +474,9 @@ pc_status pc_batch_run(pc_batch b, pc_stream s) {
         b->graph = nullptr;
         cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
         if (e != cudaSuccess) return pc_from_cuda(e);
-        cudaError_t e1 = cudaMemsetAsync(b->counter, 0, sizeof(unsigned long long), st);
         cudaError_t e2 = pc_launch_knn_batch(b->t, b->g, b->ck, b->scans_dev, b->n_scans, b->max_n, b->total_tiles,
-                                             b->tile, b->warps, b->blocks, b->k, b->eps,
-                                             b->with_cov, rho0, b->counter, st);
+                                             b->tile, b->warps, b->k, b->eps, b->with_cov, rho0, st);
         e = cudaStreamEndCapture(st, &b->graph);
-        if (e1 != cudaSuccess) e = e1;
         if (e2 != cudaSuccess) e = e2;
         if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, b->graph, 0);
         if (e != cudaSuccess) {
@@ -501,7 +492,7 @@ pc_status pc_batch_run(pc_batch b, pc_stream s) {
 
 size_t pc_batch_scratch_bytes(int n_scans) {
     if (n_scans < 1) return 0;
-    return 256 + sizeof(ScanDesc) * (size_t)n_scans;
+    return sizeof(ScanDesc) * (size_t)n_scans;
 }
 
 pc_status pc_batch_run_scratch(pc_target t, const pc_scan* scans, int n_scans, int k, float eps,
@@ -545,16 +536,12 @@ pc_status pc_batch_run_scratch(pc_target t, const pc_scan* scans, int n_scans, i
     }
     if (tiles == 0) return PC_OK;
     cudaStream_t st = (cudaStream_t)s;
-    auto* base = static_cast<unsigned char*>(scratch_dev);
-    auto* counter = reinterpret_cast<unsigned long long*>(base);
-    auto* table = reinterpret_cast<ScanDesc*>(base + 256);
-    const int blocks = pc_knn_batch_blocks(k, any_cov, warps);
+    auto* table = static_cast<ScanDesc*>(scratch_dev);
     cudaError_t e = cudaMemcpyAsync(table, hs.data(), sizeof(ScanDesc) * n_scans,
                                     cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), st);
     if (e == cudaSuccess)
-        e = pc_launch_knn_batch(t, t->g, t->ck, table, n_scans, max_n, tiles, tile, warps, blocks, k, eps, any_cov,
-                                pc_rho0(t, k), counter, st);
+        e = pc_launch_knn_batch(t, t->g, t->ck, table, n_scans, max_n, tiles, tile, warps, k, eps, any_cov,
+                                pc_rho0(t, k), st);
     return pc_from_cuda(e);
 }
 
@@ -564,7 +551,6 @@ void pc_batch_destroy(pc_batch b) {
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->graph) cudaGraphDestroy(b->graph);
     if (b->scans_dev) cudaFree(b->scans_dev);
-    if (b->counter) cudaFree(b->counter);
     b->magic = PC_MAGIC_DEAD;
     delete b;
 }

@@ -77,11 +77,9 @@ struct pc_batch_s {
     bool with_cov;
     int tile;
     int warps;
-    int blocks;
     int64_t total_tiles;
     int64_t total_queries;
     ScanDesc* scans_dev;
-    unsigned long long* counter;
     cudaGraph_t graph;
     cudaGraphExec_t exec;
     cudaStream_t captured_on;
@@ -121,14 +119,15 @@ cudaError_t pc_launch_knn(const pc_target_s* t, const float* q, int64_t N, int k
                           int32_t* idx, float* d2, float* cov, float rho0, cudaStream_t s);
 cudaError_t pc_launch_knn_union(const pc_target_s* t, const float* q, int64_t N, int k, float eps,
                                 int32_t* idx, float* d2, float* cov, float rho0, cudaStream_t s);
+// Opts the search kernels into large shared memory on the current device
+// (once; call outside any stream capture).
+cudaError_t pc_knn_prepare();
 cudaError_t pc_launch_cov(const pc_target_s* t, const int32_t* idx, int64_t N, int k, float eps,
                           float* cov, cudaStream_t s);
 cudaError_t pc_launch_knn_batch(const pc_target_s* t, const pcdev::Grid& g, const CovKernel& ck,
                                 const ScanDesc* scans_dev, int nscans, int64_t max_n,
-                                int64_t total_tiles, int tile, int warps, int blocks, int k,
-                                float eps, bool with_cov, float rho0,
-                                unsigned long long* counter, cudaStream_t s);
-int pc_knn_batch_blocks(int k, bool with_cov, int warps);
+                                int64_t total_tiles, int tile, int warps, int k, float eps,
+                                bool with_cov, float rho0, cudaStream_t s);
 
 // gicp.cu
 size_t pc_gicp_work_size();

@@ -515,7 +515,7 @@ class Target:
 
 
 class Batch:
-    """Many scans, one persistent launch replayed as a CUDA graph."""
+    """Many scans, one launch replayed as a CUDA graph."""
 
     def __init__(self, target: Target, scans, k: int, eps: float):
         """scans: list of (q [n,3] f32, idx [n,k] i32, d2 [n,k] f32, cov [n,6] f32 or None)."""

@@ -9,7 +9,7 @@ GPU).  The map's grid stays resident on the device.  The loop:
 * admits pending requests while their device bytes (scan + idx + d2 + cov)
   fit in the HBM budget, and a step slot is free;
 * launches each admitted group as ONE batched kernel (pc_batch_run_scratch)
-  on the slot's own stream: host-to-device copies, the persistent kernel and
+  on the slot's own stream: host-to-device copies, the batched kernel and
   device-to-host copies are queued on that stream, so a new step's copies
   and kernel overlap the steps already on the GPU;
 * retires steps whose completion event has fired, frees their bytes and
