@@ -21,8 +21,8 @@ BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libpc.so")
 
 SOURCES = ["knn_cov.cu", "knn_window.cu", "knn_union.cu", "knn_union_win.cu", "pc_api.cu", "grid_build.cu",
-           "noalloc.cu", "gicp.cu", "cov_weighted.cu", "wall.cu", "delta.cu"]
-HEADERS = ["pc_device.cuh", "pc_internal.h", "pc_search.cuh", "knn_kernels.cuh", "cov_weighted.cuh"]
+           "noalloc.cu", "gicp.cu", "wall.cu", "delta.cu"]
+HEADERS = ["pc_device.cuh", "pc_internal.h", "pc_search.cuh", "knn_kernels.cuh"]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # --fmad=false: no implicit contraction anywhere, so every fused multiply-add

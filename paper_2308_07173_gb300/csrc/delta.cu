@@ -1,9 +1,9 @@
-// Covariances and packing over a map that grew by pc_target_append: the
-// main grid (points 0 .. M-1) and the delta grid over the appended points
-// (M .. M+Md-1).  The search itself runs in the union kernels
-// (knn_union.cu), which visit both grids in one pass; here each neighbour
-// of a row is read from the grid that owns it, in rank order.
-#include "cov_weighted.cuh"
+// pc_cov and packing over a map that grew by pc_target_append: the main
+// grid (points 0 .. M-1) and the delta grid over the appended points
+// (M .. M+Md-1).  The search itself, with its fused covariance, runs in the
+// union kernels (knn_union.cu), which visit both grids in one pass; here
+// each neighbour of a row is read from the grid that owns it, in rank order.
+#include "knn_kernels.cuh"
 
 namespace {
 
@@ -15,23 +15,6 @@ struct Src {
         return gi < m ? __ldg(&main_xyz[gi]) : __ldg(&delta_xyz[gi - m]);
     }
 };
-
-// Kernel-descriptor weighted covariance of union rows (the search ran
-// without its fused covariance).
-__global__ void k_cov_weighted_union(Src src, CovKernel ck, const float* __restrict__ q,
-                                     const int32_t* __restrict__ idx, int64_t N, int k, float eps,
-                                     float* __restrict__ cov) {
-    const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (n >= N) return;
-    const int32_t* nb = idx + n * k;
-    float* out = cov + 6 * n;
-    if (nb[0] < 0) {
-        nan_row(out);
-        return;
-    }
-    weighted_core([&](int j) { return src.at(nb[j]); }, ck, __ldg(q + 3 * n), __ldg(q + 3 * n + 1),
-                  __ldg(q + 3 * n + 2), k, eps, out);
-}
 
 // pc_cov over the union: neighbour rows are global indices
 __global__ void k_cov_union(Src src, const int32_t* __restrict__ idx, int64_t N, int k, int64_t mtot, float eps,
@@ -67,16 +50,6 @@ __global__ void k_pack_xyz(const float4* __restrict__ main_xyz, int64_t m, const
 }
 
 }  // namespace
-
-cudaError_t pc_launch_cov_weighted_union(const pc_target_s* t, const float* q, const int32_t* idx, int64_t N,
-                                         int k, float eps, float* cov, cudaStream_t s) {
-    if (N == 0) return cudaSuccess;
-    Src src{t->g.xyz, t->delta->g.xyz, t->g.m};
-    const int threads = 128;
-    k_cov_weighted_union<<<(unsigned)((N + threads - 1) / threads), threads, 0, s>>>(src, t->ck, q, idx, N, k,
-                                                                                    eps, cov);
-    return cudaGetLastError();
-}
 
 cudaError_t pc_launch_cov_union(const pc_target_s* t, const int32_t* idx, int64_t N, int k, float eps,
                                 float* cov, cudaStream_t s) {

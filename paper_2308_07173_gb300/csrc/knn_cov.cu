@@ -79,11 +79,10 @@ cudaError_t pc_launch_knn(const pc_target_s* t, const float* q, int64_t N, int k
     if (e != cudaSuccess) return e;
     const int tile = clamp_tile(t->tune.tile);
     const int warps = clamp_warps(t->tune.warps);
-    TileArgs a{k, eps, t->tune.rho_scale > 0 ? t->tune.rho_scale : 0.9f, t->tune.order == 0 ? 1 : 0};
-    // kernel-descriptor weights: search without the covariance, then a
-    // weighted covariance pass over the neighbours
-    const bool weighted = cov != nullptr && t->ck.type != 0;
-    const bool with_cov = cov != nullptr && !weighted;
+    // the covariance (plain, or weighted by the target's kernel descriptor)
+    // is fused into the search
+    TileArgs a{k, eps, t->tune.rho_scale > 0 ? t->tune.rho_scale : 0.9f, t->tune.order == 0 ? 1 : 0, t->ck};
+    const bool with_cov = cov != nullptr;
     const int mode = search_mode(k);
     const size_t smem = (size_t)warps * warp_smem_bytes(mode);
     const int64_t tiles = (N + tile - 1) / tile;
@@ -91,11 +90,9 @@ cudaError_t pc_launch_knn(const pc_target_s* t, const float* q, int64_t N, int k
     Grid g = t->g;
     float* covp = with_cov ? cov : nullptr;
     void* args[] = {&g, (void*)&q, (void*)&N, (void*)&tile, &a, &rho0, &idx, &d2, &covp};
-    e = with_kernel<false>(mode, with_cov, g.windowed != 0, [&](void* kern) {
+    return with_kernel<false>(mode, with_cov, g.windowed != 0, [&](void* kern) {
         return cudaLaunchKernel(kern, dim3((unsigned)blocks), dim3(warps * 32), args, smem, s);
     });
-    if (e == cudaSuccess && weighted) e = pc_launch_cov_weighted(g, t->ck, q, idx, N, k, eps, cov, s);
-    return e;
 }
 
 // The union search (a target with appended points): the same launch shape
@@ -107,9 +104,8 @@ cudaError_t pc_launch_knn_union(const pc_target_s* t, const float* q, int64_t N,
     if (e != cudaSuccess) return e;
     const int tile = clamp_tile(t->tune.tile);
     const int warps = clamp_warps(t->tune.warps);
-    TileArgs a{k, eps, t->tune.rho_scale > 0 ? t->tune.rho_scale : 0.9f, t->tune.order == 0 ? 1 : 0};
-    const bool weighted = cov != nullptr && t->ck.type != 0;
-    const bool with_cov = cov != nullptr && !weighted;
+    TileArgs a{k, eps, t->tune.rho_scale > 0 ? t->tune.rho_scale : 0.9f, t->tune.order == 0 ? 1 : 0, t->ck};
+    const bool with_cov = cov != nullptr;
     const int mode = search_mode(k);
     const size_t smem = (size_t)warps * warp_smem_bytes(mode);
     const int64_t tiles = (N + tile - 1) / tile;
@@ -119,9 +115,7 @@ cudaError_t pc_launch_knn_union(const pc_target_s* t, const float* q, int64_t N,
     float* covp = with_cov ? cov : nullptr;
     void* args[] = {&g, &dg, (void*)&q, (void*)&N, (void*)&tile, &a, &rho0, &idx, &d2, &covp};
     void* kern = g.windowed ? pc_knn_union_kernel_win(mode, with_cov) : pc_knn_union_kernel(mode, with_cov);
-    e = cudaLaunchKernel(kern, dim3((unsigned)blocks), dim3(warps * 32), args, smem, s);
-    if (e == cudaSuccess && weighted) e = pc_launch_cov_weighted_union(t, q, idx, N, k, eps, cov, s);
-    return e;
+    return cudaLaunchKernel(kern, dim3((unsigned)blocks), dim3(warps * 32), args, smem, s);
 }
 
 cudaError_t pc_knn_prepare() { return ensure_attrs(); }
@@ -142,19 +136,14 @@ cudaError_t pc_launch_knn_batch(const pc_target_s* t, const Grid& gv, const CovK
     if (total_tiles == 0) return cudaSuccess;
     cudaError_t e = ensure_attrs();
     if (e != cudaSuccess) return e;
-    TileArgs a{k, eps, t->tune.rho_scale > 0 ? t->tune.rho_scale : 0.9f, t->tune.order == 0 ? 1 : 0};
+    TileArgs a{k, eps, t->tune.rho_scale > 0 ? t->tune.rho_scale : 0.9f, t->tune.order == 0 ? 1 : 0, ck};
     const int64_t blocks = (total_tiles + warps - 1) / warps;
     if (blocks > 0x7fffffff) return cudaErrorInvalidValue;
     const int mode = search_mode(k);
     const size_t smem = (size_t)warps * warp_smem_bytes(mode);
-    const bool weighted = with_cov && ck.type != 0;
-    const bool fused_cov = with_cov && !weighted;
     Grid g = gv;
     void* args[] = {&g, (void*)&scans_dev, &nscans, &total_tiles, &tile, &a, &rho0};
-    e = with_kernel<true>(mode, fused_cov, g.windowed != 0, [&](void* kern) {
+    return with_kernel<true>(mode, with_cov, g.windowed != 0, [&](void* kern) {
         return cudaLaunchKernel(kern, dim3((unsigned)blocks), dim3(warps * 32), args, smem, s);
     });
-    if (e == cudaSuccess && weighted)
-        e = pc_launch_cov_weighted_batch(g, ck, scans_dev, nscans, max_n, k, eps, s);
-    return e;
 }

@@ -483,13 +483,119 @@ __device__ void cov_row_union(const Grid& g, const Grid& dg, const int32_t* nb, 
     }, k, eps, out);
 }
 
+// Kernel-descriptor weighted covariance of one neighbourhood (Sec. III-C1:
+// the covariance is computed "using the kernel descriptors" of Table I).
+// For query x = q and its k neighbours y_j in rank order:
+//   w_j = K(x, y_j),  W = sum w_j,
+//   mu = sum w_j y_j / W,  C = sum w_j (y_j - mu)(y_j - mu)^T / W,
+// then, for eps >= 0, C' = I - (1 - eps) n n^T with n the smallest-eigenvalue
+// eigenvector (the same Jacobi solver as the plain covariance).  Binary32,
+// two passes shifted by the nearest neighbour y_0 like the plain form.  A row
+// whose W is not positive and finite is NaN.  The search kernels call it in
+// place of cov_core when a descriptor is set, reading the neighbours from the
+// cell-sorted copy they already hold in cache.
+__device__ __forceinline__ float kd_weight(const CovKernel& ck, float qx, float qy, float qz, float4 p) {
+    const float dx = qx - p.x, dy = qy - p.y, dz = qz - p.z;
+    const float r2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, dx * dx));
+    switch (ck.type) {
+        case 1:  // RBF
+        case 2:  // Gaussian (s = 1 / (2 sigma^2))
+            return expf(-r2 * ck.s);
+        case 3: {  // Polynomial on coordinates relative to the bounding-box minimum
+            const float ax = qx - ck.ox, ay = qy - ck.oy, az = qz - ck.oz;
+            const float bx = p.x - ck.ox, by = p.y - ck.oy, bz = p.z - ck.oz;
+            const float dot = __fmaf_rn(az, bz, __fmaf_rn(ay, by, ax * bx));
+            return powf(__fmaf_rn(ck.alpha, dot, ck.c), ck.d);
+        }
+        case 4: {  // histogram intersection, same relative coordinates
+            const float ax = qx - ck.ox, ay = qy - ck.oy, az = qz - ck.oz;
+            const float bx = p.x - ck.ox, by = p.y - ck.oy, bz = p.z - ck.oz;
+            return (fminf(ax, bx) + fminf(ay, by) + fminf(az, bz)) / (ax + ay + az);
+        }
+        case 5:  // Laplacian (s = 1 / sigma)
+            return expf(-sqrtf(r2) * ck.s);
+    }
+    return 1.0f;
+}
+
+template <typename G>
+__device__ void weighted_core(G&& get, const CovKernel& ck, float qx, float qy, float qz, int k, float eps,
+                              float* out) {
+    if (!isfinite(qx) || !isfinite(qy) || !isfinite(qz)) {
+        nan_row(out);
+        return;
+    }
+    const float4 p0 = get(0);
+    float W = 0.0f, sx = 0.0f, sy = 0.0f, sz = 0.0f;
+    for (int j = 0; j < k; ++j) {
+        const float4 p = get(j);
+        const float w = kd_weight(ck, qx, qy, qz, p);
+        W = W + w;
+        sx = __fmaf_rn(w, p.x - p0.x, sx);
+        sy = __fmaf_rn(w, p.y - p0.y, sy);
+        sz = __fmaf_rn(w, p.z - p0.z, sz);
+    }
+    if (!(W > 0.0f) || !isfinite(W)) {
+        nan_row(out);
+        return;
+    }
+    const float mx = sx / W, my = sy / W, mz = sz / W;
+    float cxx = 0.0f, cxy = 0.0f, cxz = 0.0f, cyy = 0.0f, cyz = 0.0f, czz = 0.0f;
+    for (int j = 0; j < k; ++j) {
+        const float4 p = get(j);
+        const float w = kd_weight(ck, qx, qy, qz, p);
+        const float dx = (p.x - p0.x) - mx, dy = (p.y - p0.y) - my, dz = (p.z - p0.z) - mz;
+        const float wx = w * dx, wy = w * dy;
+        cxx = __fmaf_rn(wx, dx, cxx);
+        cxy = __fmaf_rn(wx, dy, cxy);
+        cxz = __fmaf_rn(wx, dz, cxz);
+        cyy = __fmaf_rn(wy, dy, cyy);
+        cyz = __fmaf_rn(wy, dz, cyz);
+        czz = __fmaf_rn(w * dz, dz, czz);
+    }
+    cxx = cxx / W; cxy = cxy / W; cxz = cxz / W;
+    cyy = cyy / W; cyz = cyz / W; czz = czz / W;
+    if (eps < 0.0f) {
+        out[0] = cxx; out[1] = cxy; out[2] = cxz; out[3] = cyy; out[4] = cyz; out[5] = czz;
+        return;
+    }
+    const float3 n = min_eigvec(cxx, cxy, cxz, cyy, cyz, czz);
+    const float f = 1.0f - eps;
+    out[0] = 1.0f - f * n.x * n.x;
+    out[1] = -f * n.x * n.y;
+    out[2] = -f * n.x * n.z;
+    out[3] = 1.0f - f * n.y * n.y;
+    out[4] = -f * n.y * n.z;
+    out[5] = 1.0f - f * n.z * n.z;
+}
+
 // ---------------------------------------------------------------- tiles
 struct TileArgs {
     int k;
     float eps;
     float rho_scale;
     int last_first;  // issue tiles from the end of the query array
+    CovKernel ck;    // kernel-descriptor weights; type 0: the plain covariance
 };
+
+// The covariance of a written row (caller or union indices; a leading -1
+// marks an unanswered row), plain or weighted by the descriptor in a.
+template <bool DEL>
+__device__ void cov_row_any(const Grid& g, const Grid& dg, const int32_t* nb, int k, const TileArgs& a, float qx,
+                            float qy, float qz, float* out) {
+    if (a.ck.type == 0) {
+        cov_row_union<DEL>(g, dg, nb, k, a.eps, out);
+        return;
+    }
+    if (nb[0] < 0) {
+        nan_row(out);
+        return;
+    }
+    weighted_core([&](int j) {
+        const int64_t i = nb[j];
+        return (!DEL || i < g.m) ? __ldg(&g.xyz[i]) : __ldg(&dg.xyz[i - g.m]);
+    }, a.ck, qx, qy, qz, k, a.eps, out);
+}
 
 // Per-warp shared memory: 64 staged survivor keys of the warp-cooperative
 // search, then the lane path's survivor lists: 32 slots x 32 lanes of
@@ -830,10 +936,13 @@ __device__ void lane_tile(const Grid& g, const Grid& dg, const float* __restrict
     }
     if (COV && cov != nullptr) {
         __syncwarp();  // orders the idx rows written by other lanes
-        if (m > 0)  // neighbours straight from the cell-sorted copy, in rank order
-            cov_core([&](int j) { return pt_at<DEL>(g, dg, posl[j * 32 + lane]); }, k, a.eps, cov + 6 * n);
-        else if (active)
-            cov_row_union<DEL>(g, dg, idx + n * k, k, a.eps, cov + 6 * n);
+        if (m > 0) {  // neighbours straight from the cell-sorted copy, in rank order
+            auto get = [&](int j) { return pt_at<DEL>(g, dg, posl[j * 32 + lane]); };
+            if (a.ck.type != 0) weighted_core(get, a.ck, qx, qy, qz, k, a.eps, cov + 6 * n);
+            else cov_core(get, k, a.eps, cov + 6 * n);
+        } else if (active) {
+            cov_row_any<DEL>(g, dg, idx + n * k, k, a, qx, qy, qz, cov + 6 * n);
+        }
     }
     __syncwarp();
 }
@@ -878,7 +987,11 @@ __device__ void warp_tile(const Grid& g, const Grid& dg, const float* __restrict
     }
     if (COV && cov != nullptr) {
         __syncwarp();
-        if (lane < cnt) cov_row_union<DEL>(g, dg, idx + (n0 + lane) * k, k, a.eps, cov + 6 * (n0 + lane));
+        if (lane < cnt) {
+            const int64_t nl = n0 + lane;
+            cov_row_any<DEL>(g, dg, idx + nl * k, k, a, __ldg(q + 3 * nl), __ldg(q + 3 * nl + 1),
+                             __ldg(q + 3 * nl + 2), cov + 6 * nl);
+        }
         __syncwarp();
     }
 }

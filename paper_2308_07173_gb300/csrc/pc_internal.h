@@ -148,17 +148,7 @@ cudaError_t pc_knn_union_win_attrs();
 // delta.cu: covariances and packing over the main grid plus the delta grid
 cudaError_t pc_launch_cov_union(const pc_target_s* t, const int32_t* idx, int64_t N, int k, float eps,
                                 float* cov, cudaStream_t s);
-cudaError_t pc_launch_cov_weighted_union(const pc_target_s* t, const float* q, const int32_t* idx, int64_t N,
-                                         int k, float eps, float* cov, cudaStream_t s);
 cudaError_t pc_launch_pack_xyz(const pc_target_s* t, float* out, cudaStream_t s);
-
-// cov_weighted.cu
-cudaError_t pc_launch_cov_weighted(const pcdev::Grid& g, const CovKernel& ck, const float* q,
-                                   const int32_t* idx, int64_t N, int k, float eps, float* cov,
-                                   cudaStream_t s);
-cudaError_t pc_launch_cov_weighted_batch(const pcdev::Grid& g, const CovKernel& ck,
-                                         const ScanDesc* scans_dev, int nscans, int64_t max_n, int k,
-                                         float eps, cudaStream_t s);
 
 // pc_api.cu
 float pc_rho0(const pc_target_s* t, int k);
