@@ -14,8 +14,10 @@
 //
 // Per pair the arithmetic is binary32 (Omega by adjugate / determinant);
 // the 29 sums (H upper triangle, b, E, pair count) are added over a warp in
-// binary32, over warps, blocks and the grid in binary64, always in the same
-// order, so a launch is bit-reproducible.  The last block to finish adds the
+// binary32 by a reduce-scatter (five halving exchanges, after which lane j
+// holds the warp total of sum j: 31 shuffles where one butterfly per sum
+// takes 145), over warps, blocks and the grid in binary64, always in the
+// same order, so a launch is bit-reproducible.  The last block to finish adds the
 // block partials (a ticket counter in the caller's workspace).
 //
 // A second kernel solves (H + lambda I) xi = -b in binary64 (Cholesky) and
@@ -122,7 +124,7 @@ __device__ int nearest_within(const Grid& g, float px, float py, float pz, float
 // definite by its binary32 determinant); returns whether it counted.
 __device__ __forceinline__ bool pair_terms(const float* R, float px, float py, float pz, float4 q,
                                            const float* __restrict__ cq, const float* __restrict__ cp,
-                                           float (&v)[GICP_VALS]) {
+                                           float (&v)[32]) {
     // S = C_q + R C_p R^T (symmetric; C packed xx xy xz yy yz zz)
     const float Cp[3][3] = {{cp[0], cp[1], cp[2]}, {cp[1], cp[3], cp[4]}, {cp[2], cp[4], cp[5]}};
     float M[3][3];
@@ -210,9 +212,9 @@ __global__ void __launch_bounds__(GICP_THREADS) k_gicp_linearize(
     const int64_t stride = (int64_t)gridDim.x * GICP_THREADS;
     for (int64_t base = (int64_t)blockIdx.x * GICP_THREADS + warp * 32; base < n; base += stride) {
         const int64_t i = base + lane;
-        float v[GICP_VALS];
+        float v[32];
 #pragma unroll
-        for (int j = 0; j < GICP_VALS; ++j) v[j] = 0.0f;
+        for (int j = 0; j < 32; ++j) v[j] = 0.0f;
         if (i < n) {
             const float sx = __ldg(src + 3 * i), sy = __ldg(src + 3 * i + 1), sz = __ldg(src + 3 * i + 2);
             const float px = __fmaf_rn(R[2], sz, __fmaf_rn(R[1], sy, __fmaf_rn(R[0], sx, t[0])));
@@ -243,13 +245,20 @@ __global__ void __launch_bounds__(GICP_THREADS) k_gicp_linearize(
             }
             if (corr) corr[i] = pair;
         }
+        // Reduce-scatter across the warp: at each halving step a lane keeps
+        // half of its values (by its lane bit) and adds the partner's copy
+        // of them; after five steps lane j holds the warp total of value j.
 #pragma unroll
-        for (int j = 0; j < GICP_VALS; ++j) {
-            float x = v[j];
+        for (int half = 16; half > 0; half >>= 1) {
+            const bool upper = (lane & half) != 0;
 #pragma unroll
-            for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(FULL, x, off);
-            if (lane == j) acc += (double)x;
+            for (int j = 0; j < half; ++j) {
+                const float send = upper ? v[j] : v[j + half];
+                const float keep = upper ? v[j + half] : v[j];
+                v[j] = keep + __shfl_xor_sync(FULL, send, half);
+            }
         }
+        if (lane < GICP_VALS) acc += (double)v[0];
     }
     red[warp][lane] = acc;
     __syncthreads();
