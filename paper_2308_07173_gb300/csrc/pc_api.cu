@@ -151,8 +151,12 @@ size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 }  // namespace
 
 // A target (grid + calibration) that is not yet a registered handle.
+// Builds a target over xyz.  With `like` (the grid of appended points), the
+// cell edge and the starting radii are taken from that target instead of
+// the cell-size bisection and the calibration search: both grids are then
+// searched with one trial radius, and an append costs one grid build.
 static pc_status build_target_internal(const float* xyz, int64_t M, const pc_build_opts& o, cudaStream_t st,
-                                       pc_target_s** out) {
+                                       pc_target_s** out, const pc_target_s* like = nullptr) {
     pc_target_s* t = new (std::nothrow) pc_target_s();
     if (!t) return PC_ERR_OOM;
     std::memset(t, 0, sizeof(*t));
@@ -160,8 +164,13 @@ static pc_status build_target_internal(const float* xyz, int64_t M, const pc_bui
     cudaGetDevice(&t->device);
     t->opts = o;
     default_tune(&t->tune);
-    pc_status r = pc_build_grid(xyz, M, o, st, t);
-    if (r == PC_OK) r = calibrate_rho(t, st);
+    pc_build_opts ob = o;
+    if (like) ob.cell_size = like->g.h;
+    pc_status r = pc_build_grid(xyz, M, ob, st, t);
+    if (r == PC_OK) {
+        if (like) std::memcpy(t->rho_hint, like->rho_hint, sizeof(t->rho_hint));
+        else r = calibrate_rho(t, st);
+    }
     if (r != PC_OK) {
         cudaStreamSynchronize(st);
         pc_free_grid(t);
@@ -647,7 +656,7 @@ pc_status pc_target_append(pc_target t, const float* xyz_dev, int64_t n, pc_stre
     if (e != cudaSuccess) return pc_from_cuda(e);
     // the delta grid over every appended point (the main grid is untouched)
     pc_target_s* d = nullptr;
-    r = build_target_internal(t->delta_xyz, tot, t->opts, st, &d);
+    r = build_target_internal(t->delta_xyz, tot, t->opts, st, &d, t);
     if (r != PC_OK) return r;  // e.g. a non-finite point: nothing appended
     d->tune = t->tune;
     d->g.status = t->g.status;  // conditions of the delta search report on the handle
