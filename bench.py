@@ -64,17 +64,47 @@ def peaks():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-def measured_traffic():
-    """dram bytes per launch of the search kernel from a committed ncu
-    summary, valid only while the kernel source is unchanged."""
+def measured_profile():
+    """The committed ncu capture of the search kernel (dram bytes and warp
+    instructions per launch), valid only while the kernel source is
+    unchanged; None otherwise."""
     try:
         with open(TRAFFIC_FILE) as f:
             d = json.load(f)
         if d.get("source_sha") != kernel_source_hash():
             return None
-        return float(d["dram_bytes_per_launch_full_size"])
+        return d
     except Exception:
         return None
+
+
+def measured_traffic():
+    """dram bytes per launch of the search kernel (committed capture)."""
+    d = measured_profile()
+    try:
+        return float(d["dram_bytes_per_launch_full_size"]) if d else None
+    except (KeyError, TypeError, ValueError):
+        return None
+
+
+def issue_roofline(ms_per_launch, clk, sms):
+    """Instruction-issue roofline of the search kernel: its warp
+    instructions per launch (committed capture) over the measured launch
+    time, against 4 warp instructions per cycle per SM (one issue slot per
+    sub-partition) at the median SM clock sampled during the timed region."""
+    d = measured_profile()
+    try:
+        inst = float(d["warp_instructions_per_launch"]) if d else None
+    except (KeyError, TypeError, ValueError):
+        inst = None
+    mhz = (clk or {}).get("sm_mhz") or (clk or {}).get("sm_max_mhz")
+    if inst is None or not mhz or not sms:
+        return None
+    achieved = inst / (ms_per_launch / 1e3) / 1e12
+    peak = 4.0 * sms * mhz * 1e6 / 1e12
+    return {"bound": "issue", "achieved": achieved, "peak": peak, "unit": "Twarp-inst/s",
+            "frac": achieved / peak, "warp_instructions_per_launch": inst, "sm_count": sms, "sm_mhz": mhz,
+            "source": "smsp__inst_executed.sum of the committed ncu capture (profiles/knn_cov_c2_ncu.json)"}
 
 
 class Clocks:
@@ -355,6 +385,8 @@ def run_c2(args):
                          "kernel": "k_knn<0,1,0> (fused search + covariance, whole-map variant)"},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 12 * N,
                     "d2h_bytes_per_step": N * (8 * K_NN + 24)},
+            "issue_roofline": issue_roofline(ms_per_step, clk,
+                                             torch.cuda.get_device_properties(dev).multi_processor_count),
             "clocks": clk,
             "search_paths": {"queries": path_stats["queries"],
                              "warp_search_frac": path_stats["warp_search"] / max(1, path_stats["queries"]),
