@@ -13,8 +13,8 @@
 //   contiguous point range per row) and counts points under eight trial
 //   radii; the smallest radius holding >= k (and <= the survivor cap)
 //   wins, a failing lane retries with the radii scaled, and pass 2
-//   collects the winners' positions in shared memory.  A register bitonic
-//   network sorts 32-bit keys (d2 bits with a slot tag), an exact fix-up
+//   collects the winners' positions in shared memory.  A register odd-even
+//   merge sort network sorts 32-bit keys (d2 bits with a slot tag), an exact fix-up
 //   orders equal buckets by (d2, index), and the covariance reads the k
 //   neighbours from the cell-sorted copy in rank order.
 // * Warp path (k > 32, and the lane path's leftovers; knn_search) -- one
