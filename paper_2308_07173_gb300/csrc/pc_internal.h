@@ -21,7 +21,7 @@ struct CovKernel {
     float ox, oy, oz;
 };
 
-// One scan of a batched launch, as the persistent kernel sees it.
+// One scan of a batched launch, as the batched kernel reads it from the scan table.
 struct ScanDesc {
     const float* q;
     int64_t n;

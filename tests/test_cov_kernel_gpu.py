@@ -74,6 +74,37 @@ def test_weighted_covariance_matches_oracle(scene, gpu_lib, kind, prm):
     assert np.abs(want_raw - plain_raw).max() > 1e-6 * np.abs(plain_raw).max()
 
 
+@pytest.mark.parametrize("grown", [False, True], ids=["whole", "grown"])
+def test_weighted_rows_of_the_warp_search(scene, gpu_lib, grown):
+    # k = 40 runs the warp-cooperative search, whose rows take the weighted
+    # covariance from the caller-order copies (of both grids when grown)
+    s = scene
+    k = 40
+    q = s["q"][:4000]
+    if grown:
+        t = gpu_lib.Target(dev(s["map"][:200_000]))
+        t.append(dev(s["map"][200_000:]))
+    else:
+        t = s["t"]
+    t.set_cov_kernel("laplacian", sigma=0.1)
+    try:
+        idx, _, raw = (host(x) for x in t.knn_cov(dev(q), k, -1.0))
+        _, _, reg = (host(x) for x in t.knn_cov(dev(q), k, 1e-3))
+        st = t.sync_status()
+        origin = t.info()["origin"]
+    finally:
+        t.set_cov_kernel("none")
+        if grown:
+            t.close()
+    assert st == gpu_lib.PC_OK
+    want_i, _ = oracle.knn_brute(q, s["map"], k)
+    np.testing.assert_array_equal(idx, want_i)
+    want_raw = oracle.cov_weighted(s["map"], q, idx, -1.0, "laplacian", origin=origin, sigma=0.1)
+    want_reg = oracle.cov_weighted(s["map"], q, idx, 1e-3, "laplacian", origin=origin, sigma=0.1)
+    H.check_raw_cov(raw, want_raw)
+    H.check_regularised_cov(reg, want_reg, want_raw, raw, 1e-3)
+
+
 def test_batched_equals_single_and_clear_restores(scene, gpu_lib):
     s = scene
     t = s["t"]
