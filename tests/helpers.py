@@ -3,7 +3,7 @@ import numpy as np
 
 import oracle
 
-# the benchmark spec bar for covariances: relative Frobenius error vs the binary64 oracle
+# the covariance bar: relative Frobenius error against the binary64 oracle
 COV_RTOL = 1e-5
 
 
