@@ -727,15 +727,21 @@ __device__ void lane_tile(const Grid& g, const Grid& dg, const float* __restrict
     int dlx = 0, dhx = -1, dly = 0, dhy = -1, dlz = 0, dhz = -1;
     float deta = 0.0f;
     // Up to two lane-parallel attempts: a lane whose largest trial radius
-    // held fewer than k points retries with the radii x1.8, one whose
-    // smallest held more than CAP retries with them x0.7; only lanes that
-    // still fail go to the warp search.
+    // held fewer than k points retries with the radii x1.8.  A lane whose
+    // count jumped from below k at one radius to above CAP at the next (a
+    // wall entering the ball between two rungs) retries with thresholds
+    // spaced evenly in d2 between those two radii, where a surface's count
+    // grows evenly; one whose smallest radius held more than CAP retries
+    // with the radii x0.7.  Only lanes that still fail go to the warp
+    // search.
     float rho = rho0;
+    float rlo2 = 0.0f, rhi2 = -1.0f;  // the interval to subdivide (squared radii), rhi2 > 0
     bool todo = finite;
     for (int attempt = 0; attempt < 2 && __any_sync(FULL, todo); ++attempt) {
         if (todo) {
             todo = false;
-            const float rmax = rho * rad_mul(NRAD - 1);
+            const bool refine = rhi2 > 0.0f;
+            const float rmax = refine ? sqrtf(rhi2) : rho * rad_mul(NRAD - 1);
             const int ulx = cell_of(__fsub_rn(qx, rmax), g.ox, g.inv_h);
             const int uhx = cell_of(__fadd_rn(qx, rmax), g.ox, g.inv_h);
             const int uly = cell_of(__fsub_rn(qy, rmax), g.oy, g.inv_h);
@@ -783,7 +789,8 @@ __device__ void lane_tile(const Grid& g, const Grid& dg, const float* __restrict
 #pragma unroll
                 for (int j = 0; j < NRAD; ++j) {
                     const float r = rho * rad_mul(j);
-                    t[j] = fminf(r * r, tau);
+                    const float tr = refine ? rlo2 + (rhi2 - rlo2) * ((float)(j + 1) / (float)NRAD) : r * r;
+                    t[j] = fminf(tr, tau);
                     c[j] = 0;
                 }
                 auto count = [&](uint32_t, const float4 p) {
@@ -805,18 +812,27 @@ __device__ void lane_tile(const Grid& g, const Grid& dg, const float* __restrict
                 for (int j = NRAD - 1; j >= 0; --j)
                     if (c[j] >= k) js = j;
                 int cj = 0;
-                float tj = -1.0f;
+                float tj = -1.0f, tl = -1.0f;
 #pragma unroll
-                for (int j = 0; j < NRAD; ++j)
+                for (int j = 0; j < NRAD; ++j) {
                     if (j == js) { cj = c[j]; tj = t[j]; }
+                    if (j + 1 == js) tl = t[j];
+                }
                 if (js < 0 || cj > CAP) {
                     fallback = true;
-                    // too few within the certified radii: widen; too many: narrow
-                    // (unless the certified radius, not the trial radius, was short)
+                    // too few within the certified radii: widen; too many: subdivide
+                    // the jump or narrow (unless the certified radius, not the trial
+                    // radius, was short)
                     const bool widen = js < 0;
                     if (!(widen && t[NRAD - 1] >= tau)) {
                         todo = true;
-                        rho = widen ? rho * 1.8f : rho * 0.7f;
+                        if (!widen && js > 0 && !refine) {
+                            rlo2 = tl;
+                            rhi2 = tj;
+                        } else {
+                            rho = widen ? rho * 1.8f : rho * 0.7f;
+                            rhi2 = -1.0f;
+                        }
                     }
                 } else {
                     m = cj;
