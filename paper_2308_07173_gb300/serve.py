@@ -87,6 +87,23 @@ def _pinned_outputs(n: int, k: int):
             torch.empty((n, 6), dtype=torch.float32, pin_memory=True))
 
 
+def admit(pending: deque, used: int, budget: int, max_step: int, busy: bool, nbytes) -> tuple:
+    """One step's admission: take requests from the head of `pending` (FIFO)
+    while the step has fewer than `max_step` and their device bytes
+    (`nbytes(n)`) fit in `budget` beside the `used` bytes in flight.  A head
+    request larger than the whole budget is admitted alone when nothing is
+    in flight (`busy` false), so the queue never stalls; otherwise a request
+    that does not fit waits for retirements.  Returns (batch, used)."""
+    batch = []
+    while pending and len(batch) < max_step:
+        b = nbytes(pending[0].n)
+        if used + b > budget and (batch or busy):
+            break
+        batch.append(pending.popleft())
+        used += b
+    return batch, used
+
+
 @dataclass
 class _Step:
     slot: int
@@ -178,15 +195,9 @@ class Server:
                     inflight.remove(st)
                     done += len(st.reqs)
             if pending and free_slots:
-                batch = []
-                while pending and len(batch) < self.max_step:
-                    b = self.request_bytes(pending[0].n)
-                    if used + b > self.budget and (batch or inflight):
-                        break
-                    r = pending.popleft()
+                batch, used = admit(pending, used, self.budget, self.max_step, bool(inflight), self.request_bytes)
+                for r in batch:
                     r.t_admit = now
-                    used += b
-                    batch.append(r)
                 if batch:
                     inflight.append(self._launch(free_slots.pop(0), batch))
                     continue
