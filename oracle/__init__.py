@@ -26,8 +26,15 @@ Functions follow the plain definitions:
   (H + lam I) xi = -b, move the pose by Exp(omega) on the left.
 
 Parity of the covariance against the paper's own numbers is unpinned: the
-paper prints no worked example.  The pins live in ``tests/test_oracle_pins.py``
-(closed forms, invariants, exact rational arithmetic, library cross-checks).
+paper prints no worked example.  ``cov_weighted`` is also parity unpinned
+against the paper, which never says how a kernel descriptor enters the
+covariance: it fixes one reading (weights in the moments), pinned only by
+closed forms of that reading.  The pins live in ``tests/test_oracle_pins.py``
+(closed forms, invariants, exact rational arithmetic, library
+cross-checks), ``tests/test_oracle_gicp.py`` (finite differences, a
+Sherman-Morrison case, pose recovery), ``tests/test_oracle_kernels.py`` and
+``tests/test_oracle_wall.py`` (exact means, vote separation, breadth-first
+clustering, parabola recovery).
 """
 from __future__ import annotations
 
