@@ -70,8 +70,7 @@ def test_c1_cov_regularised_and_raw(c1, c1_oracle, gpu_lib):
     raw64 = oracle.cov(p, ref_idx, -1.0)
     reg64 = oracle.cov(p, ref_idx, 1e-3)
     H.check_raw_cov(raw, raw64)
-    frac = H.check_regularised_cov(cov_reg, reg64, raw64, raw, 1e-3)
-    assert frac > 0.95
+    H.check_regularised_cov(cov_reg, reg64, raw64, raw, 1e-3, label="C1")
 
 
 def test_fused_equals_separate_calls(c1, gpu_lib):
@@ -293,29 +292,24 @@ def c2(gpu_lib):
     t.close()
 
 
-def test_c2_full_size_sampled_parity(c2, gpu_lib):
+def test_c2_full_size_parity_every_row(c2, gpu_lib):
+    """The headline workload (131k-point scan, 2M-point map, k = 20) in the
+    launch configuration the benchmark times: every row against the oracle's
+    k-d tree -- idx and d2 bit-exact, raw and regularised covariances within
+    the per-band bar."""
     q, m, t, tree = c2
     k, eps = 20, 1e-3
     idx, d2, cov, st = run_knn_cov(gpu_lib, t, q, k, eps)
     assert st == gpu_lib.PC_OK
-    g = np.random.default_rng(0)
-    sample = np.sort(g.choice(len(q), 3000, replace=False))
-    ri, rd = tree.knn(q[sample], k)
-    np.testing.assert_array_equal(idx[sample], ri)
-    np.testing.assert_array_equal(d2[sample].view(np.uint32), rd.view(np.uint32))
+    ri, rd = tree.knn(q, k)
+    np.testing.assert_array_equal(idx, ri)
+    np.testing.assert_array_equal(d2.view(np.uint32), rd.view(np.uint32))
     raw64 = oracle.cov(m, ri, -1.0)
     reg64 = oracle.cov(m, ri, eps)
     raw = host(t.cov(dev(ri), -1.0))
     H.check_raw_cov(raw, raw64)
-    frac = H.check_regularised_cov(cov[sample], reg64, raw64, raw, eps)
-    assert frac > 0.97
-    # every row: valid, ascending keys, d2 consistent with the returned points
-    assert (idx >= 0).all() and (idx < len(m)).all()
-    key = (d2.view(np.uint32).astype(np.uint64) << np.uint64(32)) | idx.astype(np.uint64)
-    assert (np.diff(d2, axis=1) >= 0).all()
-    assert (key[:, 1:] > key[:, :-1]).all()
-    diff = q[:, None, :].astype(np.float64) - m[idx].astype(np.float64)
-    np.testing.assert_allclose(d2, (diff ** 2).sum(-1), rtol=1e-5, atol=1e-9)
+    bands = H.check_regularised_cov(cov, reg64, raw64, raw, eps, label="C2")
+    assert bands["well"]["rows"] + bands["mid"]["rows"] + bands["degenerate"]["rows"] == len(q)
 
 
 def test_c2_batch_equals_single_scans(c2, gpu_lib):
@@ -369,7 +363,7 @@ def test_uneven_occupancy_map_parity(pit_world, gpu_lib, k):
     np.testing.assert_array_equal(d2.view(np.uint32), rd.view(np.uint32))
     raw = host(t.cov(dev(ri), -1.0))
     H.check_raw_cov(raw, oracle.cov(m, ri, -1.0))
-    H.check_regularised_cov(cov, oracle.cov(m, ri, 1e-3), oracle.cov(m, ri, -1.0), raw, 1e-3)
+    H.check_regularised_cov(cov, oracle.cov(m, ri, 1e-3), oracle.cov(m, ri, -1.0), raw, 1e-3, label=f"pit k={k}")
 
 
 def test_retries_and_fallbacks_stay_exact(gpu_lib):
