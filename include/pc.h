@@ -112,7 +112,8 @@ typedef struct {
     int64_t warp_search; /* of those, answered by the warp-cooperative search
                             (k > 32, or k <= 32 queries the lane path handed over) */
     int64_t exhaustive;  /* searches that ended in the exhaustive cell scan */
-    int64_t reserved;
+    int64_t candidates;  /* target points whose distance the lane path computed
+                            (its counting and collecting passes together) */
 } pc_stats;
 
 /* One scan of a batch: device pointers, caller-owned. */
@@ -213,7 +214,8 @@ typedef struct {
  * moments are binary32 (two passes shifted by the nearest neighbour).  A row
  * whose total weight is not positive and finite (a polynomial can make it
  * so) is NaN.  The neighbours are unchanged: the search runs as without a
- * kernel and a second launch forms the weighted covariances.  NULL or type
+ * kernel, and the weighted covariance is formed in the same launch, in the
+ * search's epilogue, from the neighbours it has just found.  NULL or type
  * PC_KERNEL_NONE restores the plain covariance.  pc_cov is not affected (it
  * has no query points).  A batch plan keeps the kernel set when it was
  * planned.  Host-only.  Errors: PC_ERR_INVALID_ARG for an unknown type, a
@@ -226,11 +228,11 @@ PC_API pc_status pc_set_cov_kernel(pc_target t, const pc_cov_kernel *kd);
  * rebuilding its grid.  They get the indices M + (their position among all
  * appended points), and every later search -- pc_knn, pc_knn_cov,
  * pc_knn_cov_host, pc_cov, pc_gicp_linearize -- answers over the whole
- * union exactly: the main grid is searched as usual, then each query's row
- * is completed from a small grid over the appended points, visiting only
- * those strictly closer than the row's k-th neighbour (a certified box), so
- * results equal a target built from all the points at once (idx and d2 bit
- * for bit; the covariance to its rounding).  The delta grid is rebuilt from all appended points at
+ * union exactly: one launch searches the main grid and a small grid over
+ * the appended points together (each query's boxes on both grids, filtered
+ * by the smaller of their certified radii), so results equal a target
+ * built from all the points at once (idx and d2 bit for bit; the
+ * covariance to its rounding).  The delta grid is rebuilt from all appended points at
  * each call (O(appended) work; the main grid is never touched).  Windows and
  * covariance kernels apply to both.  The batched forms refuse a target with
  * appended points (PC_ERR_INVALID_ARG): compact it first.  Synchronous with
@@ -315,14 +317,22 @@ PC_API pc_status pc_batch_run_scratch(pc_target t, const pc_scan *scans, int n_s
  *  - n_scans < 1 or > PC_NOALLOC_MAX_SCANS returns PC_ERR_INVALID_ARG and
  *    launches nothing; other argument errors are those of pc_batch_plan.
  *  - The first call on a device looks up the array's device address (once
- *    per device, with that device current); make that first call before
- *    any stream capture.
+ *    per device, with that device current).
+ *  - It cannot be captured into a CUDA graph: the scan table is copied from
+ *    the caller's pageable host memory, which stream capture does not
+ *    allow.  On a stream that is capturing it returns PC_ERR_INVALID_ARG
+ *    and enqueues nothing, so the capture stays valid.  (pc_batch_plan and
+ *    pc_batch_run are the capturable batched form.)
  *  - Every call on a device uses the same array and it keeps the last
  *    call's scan table: calls that overlap on the GPU -- on two streams, or from two host
  *    threads -- race and corrupt each other's results.  Serialise them.
- *  - Asynchronous on `s`; the scan table is copied from the caller's host
- *    array before the call returns, so that array may be reused at once.
- *    Results are identical to pc_knn_cov on each scan alone. */
+ *  - Asynchronous on `s` apart from the table copy: the table is copied
+ *    from the caller's host array before the call returns, so that array
+ *    may be reused at once, but a copy from pageable memory may make the
+ *    host wait for work already queued on `s`.
+ *  - Results are identical to pc_knn_cov on each scan alone (idx, d2 and
+ *    cov bit for bit); a scan with n = 0 is skipped and one with cov_dev =
+ *    NULL gets no covariances. */
 PC_API pc_status pc_batch_run_noalloc(pc_target t, const pc_scan *scans, int n_scans, int k,
                                       float eps, pc_stream s);
 

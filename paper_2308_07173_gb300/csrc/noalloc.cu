@@ -3,7 +3,6 @@
 // allocate once they are running.  Nothing here allocates: the device
 // address of the array is looked up once per device, the scan table is
 // copied into it, and the existing batched launch runs on it.
-#include <cmath>
 #include <mutex>
 
 #include "pc_internal.h"
@@ -41,12 +40,9 @@ pc_status scratch_on_current_device(unsigned char** out) {
 
 extern "C" pc_status pc_batch_run_noalloc(pc_target t, const pc_scan* scans, int n_scans, int k,
                                           float eps, pc_stream s) {
+    if (!scans || n_scans < 1 || n_scans > PC_NOALLOC_MAX_SCANS) return PC_ERR_INVALID_ARG;
     if (!t) return PC_ERR_INVALID_ARG;
     if (!pc_target_is_live(t)) return PC_ERR_DESTROYED;
-    if (!scans || n_scans < 1 || n_scans > PC_NOALLOC_MAX_SCANS) return PC_ERR_INVALID_ARG;
-    if (k < 1 || k > 64 || !std::isfinite(eps)) return PC_ERR_INVALID_ARG;
-    if (t->delta) return PC_ERR_INVALID_ARG;  // appended points: pc_target_compact first
-    if ((int64_t)k > t->g.m) return PC_ERR_K_GT_M;
     int prev = -1;
     if (cudaGetDevice(&prev) != cudaSuccess) return PC_ERR_CUDA;
     if (prev != t->device && cudaSetDevice(t->device) != cudaSuccess) return PC_ERR_CUDA;
@@ -56,46 +52,25 @@ extern "C" pc_status pc_batch_run_noalloc(pc_target t, const pc_scan* scans, int
             if (dev != was) cudaSetDevice(was);
         }
     } restore{t->device, prev};
-
-    bool any_cov = false;
-    for (int i = 0; i < n_scans; ++i) {
-        const pc_scan& sc = scans[i];
-        if (sc.n < 0) return PC_ERR_INVALID_ARG;
-        if (sc.n == 0) continue;
-        if (!sc.q_dev || !sc.idx_dev || !sc.d2_dev) return PC_ERR_INVALID_ARG;
-        if (!pc_is_device_ptr(sc.q_dev) || !pc_is_device_ptr(sc.idx_dev) ||
-            !pc_is_device_ptr(sc.d2_dev))
-            return PC_ERR_BAD_POINTER;
-        if (sc.cov_dev) {
-            if (!pc_is_device_ptr(sc.cov_dev)) return PC_ERR_BAD_POINTER;
-            any_cov = true;
-        }
-    }
-    const int tile = t->tune.tile < 1 ? 32 : (t->tune.tile > 32 ? 32 : t->tune.tile);
-    const int warps = t->tune.warps < 1 ? 4 : (t->tune.warps > 8 ? 8 : t->tune.warps);
+    // A pageable host-to-device copy cannot be captured: refuse before any
+    // other CUDA call, so a caller's capture is left intact.
+    cudaStream_t st = (cudaStream_t)s;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(st, &cs);
+    if (e != cudaSuccess) return pc_from_cuda(e);
+    if (cs != cudaStreamCaptureStatusNone) return PC_ERR_INVALID_ARG;
     ScanDesc table[PC_NOALLOC_MAX_SCANS];
-    int64_t tiles = 0, max_n = 0;
-    for (int i = 0; i < n_scans; ++i) {
-        table[i].q = scans[i].q_dev;
-        table[i].n = scans[i].n;
-        table[i].idx = scans[i].idx_dev;
-        table[i].d2 = scans[i].d2_dev;
-        table[i].cov = scans[i].cov_dev;
-        table[i].tile0 = tiles;
-        tiles += (scans[i].n + tile - 1) / tile;
-        if (scans[i].n > max_n) max_n = scans[i].n;
-    }
-    if (tiles == 0) return PC_OK;
+    BatchShape sh;
+    pc_status r = pc_batch_table(t, scans, n_scans, k, eps, table, &sh);
+    if (r != PC_OK) return r;
+    if (sh.tiles == 0) return PC_OK;
 
     unsigned char* scratch = nullptr;
-    pc_status r = scratch_on_current_device(&scratch);
-    if (r != PC_OK) return r;
-    cudaStream_t st = (cudaStream_t)s;
+    if ((r = scratch_on_current_device(&scratch)) != PC_OK) return r;
     auto* table_dev = reinterpret_cast<ScanDesc*>(scratch);
-    cudaError_t e = cudaMemcpyAsync(table_dev, table, sizeof(ScanDesc) * n_scans,
-                                    cudaMemcpyHostToDevice, st);
+    e = cudaMemcpyAsync(table_dev, table, sizeof(ScanDesc) * n_scans, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess)
-        e = pc_launch_knn_batch(t, t->g, t->ck, table_dev, n_scans, max_n, tiles, tile, warps, k, eps, any_cov,
-                                pc_rho0(t, k), st);
+        e = pc_launch_knn_batch(t, t->g, t->ck, table_dev, n_scans, sh.max_n, sh.tiles, sh.tile, sh.warps, k, eps,
+                                sh.any_cov, pc_rho0(t, k), st);
     return pc_from_cuda(e);
 }

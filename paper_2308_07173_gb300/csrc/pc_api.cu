@@ -394,7 +394,7 @@ pc_status pc_get_stats(pc_target t, pc_stream s, pc_stats* out, int reset) {
     out->queries = (int64_t)v[0];
     out->warp_search = (int64_t)v[1];
     out->exhaustive = (int64_t)v[2];
-    out->reserved = (int64_t)v[3];
+    out->candidates = (int64_t)v[3];
     return PC_OK;
 }
 
@@ -499,6 +499,52 @@ pc_status pc_batch_run(pc_batch b, pc_stream s) {
     return pc_from_cuda(cudaGraphLaunch(b->exec, st));
 }
 
+}  // extern "C"
+
+// Checks shared by the batched entries that run on caller-provided scans
+// (pc_batch_run_scratch, pc_batch_run_noalloc) and the scan table they
+// copy to the device: a live target without appended points, 1 <= k <= 64,
+// k <= M, finite eps, every non-empty scan's buffers in device memory.
+pc_status pc_batch_table(const pc_target_s* t, const pc_scan* scans, int n_scans, int k, float eps,
+                         ScanDesc* table, BatchShape* shape) {
+    if (!t) return PC_ERR_INVALID_ARG;
+    if (!live(t)) return PC_ERR_DESTROYED;
+    if (!scans || n_scans < 1 || k < 1 || k > 64 || !std::isfinite(eps)) return PC_ERR_INVALID_ARG;
+    if (t->delta) return PC_ERR_INVALID_ARG;  // appended points: pc_target_compact first
+    if ((int64_t)k > t->g.m) return PC_ERR_K_GT_M;
+    BatchShape sh;
+    sh.tile = std::min(std::max(t->tune.tile, 1), 32);
+    sh.warps = std::min(std::max(t->tune.warps, 1), 8);
+    sh.tiles = 0;
+    sh.max_n = 0;
+    sh.any_cov = false;
+    for (int i = 0; i < n_scans; ++i) {
+        const pc_scan& sc = scans[i];
+        if (sc.n < 0) return PC_ERR_INVALID_ARG;
+        if (sc.n > 0) {
+            if (!sc.q_dev || !sc.idx_dev || !sc.d2_dev) return PC_ERR_INVALID_ARG;
+            if (!is_device_ptr(sc.q_dev) || !is_device_ptr(sc.idx_dev) || !is_device_ptr(sc.d2_dev))
+                return PC_ERR_BAD_POINTER;
+            if (sc.cov_dev) {
+                if (!is_device_ptr(sc.cov_dev)) return PC_ERR_BAD_POINTER;
+                sh.any_cov = true;
+            }
+        }
+        table[i].q = sc.q_dev;
+        table[i].n = sc.n;
+        table[i].idx = sc.idx_dev;
+        table[i].d2 = sc.d2_dev;
+        table[i].cov = sc.cov_dev;
+        table[i].tile0 = sh.tiles;
+        sh.tiles += (sc.n + sh.tile - 1) / sh.tile;
+        sh.max_n = std::max<int64_t>(sh.max_n, sc.n);
+    }
+    *shape = sh;
+    return PC_OK;
+}
+
+extern "C" {
+
 size_t pc_batch_scratch_bytes(int n_scans) {
     if (n_scans < 1) return 0;
     return sizeof(ScanDesc) * (size_t)n_scans;
@@ -508,49 +554,23 @@ pc_status pc_batch_run_scratch(pc_target t, const pc_scan* scans, int n_scans, i
                                void* scratch_dev, size_t scratch_bytes, pc_stream s) {
     pc_status r = check_target(t);
     if (r != PC_OK) return r;
-    if (!scans || n_scans < 1 || k < 1 || k > 64 || !std::isfinite(eps)) return PC_ERR_INVALID_ARG;
-    if (t->delta) return PC_ERR_INVALID_ARG;  // appended points: pc_target_compact first
-    if ((int64_t)k > t->g.m) return PC_ERR_K_GT_M;
+    if (!scans || n_scans < 1) return PC_ERR_INVALID_ARG;
+    std::vector<ScanDesc> hs(n_scans);
+    BatchShape sh;
+    if ((r = pc_batch_table(t, scans, n_scans, k, eps, hs.data(), &sh)) != PC_OK) return r;
     if (!scratch_dev || (reinterpret_cast<uintptr_t>(scratch_dev) & 255u) ||
         scratch_bytes < pc_batch_scratch_bytes(n_scans))
         return PC_ERR_INVALID_ARG;
     if (!is_device_ptr(scratch_dev)) return PC_ERR_BAD_POINTER;
-    bool any_cov = false;
-    for (int i = 0; i < n_scans; ++i) {
-        const pc_scan& sc = scans[i];
-        if (sc.n < 0) return PC_ERR_INVALID_ARG;
-        if (sc.n == 0) continue;
-        if (!sc.q_dev || !sc.idx_dev || !sc.d2_dev) return PC_ERR_INVALID_ARG;
-        if (!is_device_ptr(sc.q_dev) || !is_device_ptr(sc.idx_dev) || !is_device_ptr(sc.d2_dev))
-            return PC_ERR_BAD_POINTER;
-        if (sc.cov_dev) {
-            if (!is_device_ptr(sc.cov_dev)) return PC_ERR_BAD_POINTER;
-            any_cov = true;
-        }
-    }
+    if (sh.tiles == 0) return PC_OK;
     DeviceGuard dg(t->device);
-    const int tile = std::min(std::max(t->tune.tile, 1), 32);
-    const int warps = std::min(std::max(t->tune.warps, 1), 8);
-    std::vector<ScanDesc> hs(n_scans);
-    int64_t tiles = 0, max_n = 0;
-    for (int i = 0; i < n_scans; ++i) {
-        hs[i].q = scans[i].q_dev;
-        hs[i].n = scans[i].n;
-        hs[i].idx = scans[i].idx_dev;
-        hs[i].d2 = scans[i].d2_dev;
-        hs[i].cov = scans[i].cov_dev;
-        hs[i].tile0 = tiles;
-        tiles += (scans[i].n + tile - 1) / tile;
-        max_n = std::max<int64_t>(max_n, scans[i].n);
-    }
-    if (tiles == 0) return PC_OK;
     cudaStream_t st = (cudaStream_t)s;
     auto* table = static_cast<ScanDesc*>(scratch_dev);
     cudaError_t e = cudaMemcpyAsync(table, hs.data(), sizeof(ScanDesc) * n_scans,
                                     cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess)
-        e = pc_launch_knn_batch(t, t->g, t->ck, table, n_scans, max_n, tiles, tile, warps, k, eps, any_cov,
-                                pc_rho0(t, k), st);
+        e = pc_launch_knn_batch(t, t->g, t->ck, table, n_scans, sh.max_n, sh.tiles, sh.tile, sh.warps, k, eps,
+                                sh.any_cov, pc_rho0(t, k), st);
     return pc_from_cuda(e);
 }
 

@@ -152,6 +152,17 @@ cudaError_t pc_launch_pack_xyz(const pc_target_s* t, float* out, cudaStream_t s)
 
 // pc_api.cu
 float pc_rho0(const pc_target_s* t, int k);
+// Launch shape of a batched call over caller-provided scans.
+struct BatchShape {
+    int64_t tiles;  // work items (tiles of `tile` queries) over all scans; 0: nothing to do
+    int64_t max_n;  // largest scan
+    int tile, warps;
+    bool any_cov;   // some scan asks for covariances
+};
+// Argument checks and scan table shared by pc_batch_run_scratch and
+// pc_batch_run_noalloc; fills table[0, n_scans).
+pc_status pc_batch_table(const pc_target_s* t, const pc_scan* scans, int n_scans, int k, float eps,
+                         ScanDesc* table, BatchShape* shape);
 pc_status pc_from_cuda(cudaError_t e);
 bool pc_target_is_live(const pc_target_s* t);
 bool pc_is_device_ptr(const void* p);
