@@ -27,11 +27,26 @@ from . import pc
 FLUSH_BYTES = 256 << 20
 
 
+PKG = os.path.dirname(os.path.abspath(__file__))
+
+
+def default_cache() -> str:
+    """The package's cache of tuned configurations (JSON), consulted by the
+    batched and served forms when they are given no configuration."""
+    return os.path.join(PKG, "tune_cache.json")
+
+
+def n_bucket(n: int) -> int:
+    """Query counts share a cache entry within a power of two (0: any)."""
+    n = int(n)
+    return 0 if n <= 0 else 1 << (n - 1).bit_length()
+
+
 def _key(k: int, m: int, n: int) -> str:
     import torch
 
     name = torch.cuda.get_device_name().replace(" ", "_")
-    return f"{name}|k{k}|m{m}|n{n}"
+    return f"{name}|k{k}|m{m}|n{n_bucket(n)}"
 
 
 def load_cache(path: str) -> dict:

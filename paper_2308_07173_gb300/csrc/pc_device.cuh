@@ -47,7 +47,8 @@ struct Grid {
     const uint32_t* occ;
     const uint32_t* rank;
     int* status;
-    unsigned long long* stats;  // [0] queries, [1] warp-search fallbacks, [2] exhaustive scans
+    unsigned long long* stats;  // [0] queries, [1] warp-search fallbacks, [2] exhaustive scans,
+                                // [3] lane-path candidate points
     // Search window (pc_set_window): only target points p with
     // wlo <= p <= whi (componentwise) are searched.  [wl, wh] is the range of
     // cells that can hold them (the whole grid when windowed == 0); a point

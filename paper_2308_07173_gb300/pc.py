@@ -112,7 +112,7 @@ class pc_target_info(ctypes.Structure):
 
 class pc_stats(ctypes.Structure):
     _fields_ = [("queries", ctypes.c_int64), ("warp_search", ctypes.c_int64),
-                ("exhaustive", ctypes.c_int64), ("reserved", ctypes.c_int64)]
+                ("exhaustive", ctypes.c_int64), ("candidates", ctypes.c_int64)]
 
 
 class pc_scan(ctypes.Structure):
@@ -497,7 +497,8 @@ class Target:
 
     def stats(self, reset: bool = False, stream=None) -> dict:
         st = pc_get_stats(self.handle, _stream_handle(stream), reset)
-        return {"queries": st.queries, "warp_search": st.warp_search, "exhaustive": st.exhaustive}
+        return {"queries": st.queries, "warp_search": st.warp_search, "exhaustive": st.exhaustive,
+                "candidates": st.candidates}
 
     def sync_status(self, stream=None) -> int:
         return pc_sync_status(self.handle, _stream_handle(stream))

@@ -6,8 +6,10 @@ GPU).  The map's grid stays resident on the device.  The loop:
 
 * moves arrived requests to a pending queue (arrival times are replayed in
   real time, optionally sped up);
-* admits pending requests while their device bytes (scan + idx + d2 + cov)
-  fit in the HBM budget, and a step slot is free;
+* admits pending requests while their device bytes (scan + idx + d2 + cov,
+  each rounded up to the caching allocator's 512-byte blocks) fit in the
+  HBM budget left after the step slots' fixed scratch, and a step slot is
+  free;
 * launches each admitted group as ONE batched kernel (pc_batch_run_scratch)
   on the slot's own stream: host-to-device copies, the batched kernel and
   device-to-host copies are queued on that stream, so a new step's copies
@@ -104,6 +106,13 @@ def admit(pending: deque, used: int, budget: int, max_step: int, busy: bool, nby
     return batch, used
 
 
+ALLOC_BLOCK = 512  # torch's caching allocator rounds every block up to this
+
+
+def _blocks(nbytes: int) -> int:
+    return -(-int(nbytes) // ALLOC_BLOCK) * ALLOC_BLOCK
+
+
 @dataclass
 class _Step:
     slot: int
@@ -130,11 +139,17 @@ class Server:
         self.scratch_bytes = pc.pc_batch_scratch_bytes(self.max_step)
         self.scratch = [torch.empty(self.scratch_bytes, dtype=torch.uint8, device=self.dev)
                         for _ in range(slots)]
+        # the slots' scan tables are held for the server's lifetime: the
+        # requests share what is left of the budget
+        self.fixed_bytes = slots * _blocks(self.scratch_bytes)
+        self.request_budget = max(0, self.budget - self.fixed_bytes)
         self.steps_launched = 0
         self.keep = keep_results
 
     def request_bytes(self, n: int) -> int:
-        return n * (12 + 8 * self.k + 24)
+        """Device bytes one request holds while in flight: its scan, idx, d2
+        and cov tensors, each rounded up to the allocator's block size."""
+        return (_blocks(12 * n) + _blocks(4 * self.k * n) + _blocks(4 * self.k * n) + _blocks(24 * n))
 
     def _launch(self, slot: int, reqs: List[Request]) -> _Step:
         import torch
@@ -170,6 +185,8 @@ class Server:
         for r in reqs:
             r.t_sched = r.t_arrival / speed
         self.steps_launched = 0
+        waited = set()
+        peak = 0
         pending: deque = deque()
         inflight: List[_Step] = []
         free_slots = list(range(len(self.streams)))
@@ -195,9 +212,13 @@ class Server:
                     inflight.remove(st)
                     done += len(st.reqs)
             if pending and free_slots:
-                batch, used = admit(pending, used, self.budget, self.max_step, bool(inflight), self.request_bytes)
+                batch, used = admit(pending, used, self.request_budget, self.max_step, bool(inflight),
+                                    self.request_bytes)
+                peak = max(peak, used)
                 for r in batch:
                     r.t_admit = now
+                if not batch and pending[0].rid not in waited:
+                    waited.add(pending[0].rid)  # the head request waits for bytes to be freed
                 if batch:
                     inflight.append(self._launch(free_slots.pop(0), batch))
                     continue
@@ -209,6 +230,9 @@ class Server:
         out = latency_report(reqs, wall)
         out["steps"] = self.steps_launched
         out["mean_scans_per_step"] = len(reqs) / max(1, self.steps_launched)
+        out["admission_waits"] = len(waited)  # requests that waited for budget
+        out["peak_request_bytes"] = peak
+        out["request_budget"] = self.request_budget
         return out
 
 

@@ -90,3 +90,25 @@ def test_tiny_budget_serves_one_scan_at_a_time(small_world, gpu_lib):
     assert rep["scans"] == 10 and rep["steps"] == 10  # the budget admits one request per step
     for r in reqs:
         assert _same(r.out_host, _alone(t, r.points, k, eps))
+
+
+def test_budget_that_forces_waits(small_world, gpu_lib):
+    """A budget with room for about two requests beside the slots' scratch:
+    requests that arrive together wait for earlier ones to retire, the bytes
+    in flight never exceed the budget, and every result is still the one the
+    scan gets alone."""
+    t, arr = small_world
+    k, eps = 20, 1e-3
+    reqs = serve.requests_from_arrivals(arr)
+    serve.prepare(reqs)
+    probe = serve.Server(t, k, eps, hbm_budget=1 << 30, max_step_scans=4, slots=2)
+    biggest = max(probe.request_bytes(r.n) for r in reqs)
+    budget = probe.fixed_bytes + int(2.2 * biggest)
+    srv = serve.Server(t, k, eps, hbm_budget=budget, max_step_scans=4, slots=2, keep_results=True)
+    rep = srv.serve(reqs, speed=1e6)
+    assert rep["scans"] == len(reqs)
+    assert rep["admission_waits"] > 0
+    assert rep["peak_request_bytes"] <= srv.request_budget
+    for r in reqs:
+        assert _same(r.out_host, _alone(t, r.points, k, eps))
+    assert t.sync_status() == gpu_lib.PC_OK
