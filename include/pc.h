@@ -88,6 +88,10 @@ typedef struct {
                           <= 0: 0.9 */
     int order;         /* 0: issue query tiles last-first (a ring-by-ring LiDAR scan ends
                           with its slowest, farthest rings); 1: first-first */
+    int probe;         /* where each query's trial radii start (k <= 32): 0 auto (1 on a
+                          map whose calibration saw an even density, else 2); 1 the
+                          calibrated radius for every query; 2 a per-query radius from
+                          the point count of the 27 cells around it */
 } pc_tune;
 
 /* What the built target looks like (for reporting and tuning). */

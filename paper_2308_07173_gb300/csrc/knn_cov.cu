@@ -81,7 +81,8 @@ cudaError_t pc_launch_knn(const pc_target_s* t, const float* q, int64_t N, int k
     const int warps = clamp_warps(t->tune.warps);
     // the covariance (plain, or weighted by the target's kernel descriptor)
     // is fused into the search
-    TileArgs a{k, eps, t->tune.rho_scale > 0 ? t->tune.rho_scale : 0.9f, t->tune.order == 0 ? 1 : 0, t->ck};
+    TileArgs a{k, eps, t->tune.rho_scale > 0 ? t->tune.rho_scale : 0.9f, t->tune.order == 0 ? 1 : 0, t->ck,
+               pc_probe_c(t)};
     const bool with_cov = cov != nullptr;
     const int mode = search_mode(k);
     const size_t smem = (size_t)warps * warp_smem_bytes(mode);
@@ -104,7 +105,8 @@ cudaError_t pc_launch_knn_union(const pc_target_s* t, const float* q, int64_t N,
     if (e != cudaSuccess) return e;
     const int tile = clamp_tile(t->tune.tile);
     const int warps = clamp_warps(t->tune.warps);
-    TileArgs a{k, eps, t->tune.rho_scale > 0 ? t->tune.rho_scale : 0.9f, t->tune.order == 0 ? 1 : 0, t->ck};
+    TileArgs a{k, eps, t->tune.rho_scale > 0 ? t->tune.rho_scale : 0.9f, t->tune.order == 0 ? 1 : 0, t->ck,
+               pc_probe_c(t)};
     const bool with_cov = cov != nullptr;
     const int mode = search_mode(k);
     const size_t smem = (size_t)warps * warp_smem_bytes(mode);
@@ -136,7 +138,8 @@ cudaError_t pc_launch_knn_batch(const pc_target_s* t, const Grid& gv, const CovK
     if (total_tiles == 0) return cudaSuccess;
     cudaError_t e = ensure_attrs();
     if (e != cudaSuccess) return e;
-    TileArgs a{k, eps, t->tune.rho_scale > 0 ? t->tune.rho_scale : 0.9f, t->tune.order == 0 ? 1 : 0, ck};
+    TileArgs a{k, eps, t->tune.rho_scale > 0 ? t->tune.rho_scale : 0.9f, t->tune.order == 0 ? 1 : 0, ck,
+               pc_probe_c(t)};
     const int64_t blocks = (total_tiles + warps - 1) / warps;
     if (blocks > 0x7fffffff) return cudaErrorInvalidValue;
     const int mode = search_mode(k);

@@ -306,41 +306,48 @@ __device__ int knn_search(const Grid& g, const Grid& dg, float qx, float qy, flo
 
 // ---------------------------------------------------------------- covariance
 
-// One Jacobi rotation in the (p,q) plane that zeroes a_pq of a symmetric
-// matrix (r is the remaining index): with theta = (a_qq - a_pp) / (2 a_pq)
-// and t the smaller root of t^2 + 2 t theta - 1 = 0, c = 1/sqrt(1+t^2),
-// s = t c, the diagonal moves by -+ t a_pq and the r-row and the
-// eigenvector columns p, q rotate by (c, s) (Golub & Van Loan, sec. 8.5).
-__host__ __device__ __forceinline__ void jacobi_rotate(float& app, float& aqq, float& apq, float& arp,
-                                              float& arq, float& v0p, float& v0q, float& v1p,
-                                              float& v1q, float& v2p, float& v2q) {
-    if (apq == 0.0f) return;
-    const float theta = (aqq - app) / (2.0f * apq);
-    const float at = fabsf(theta);
-    const float t = at > 1e18f ? 0.5f / theta
-                               : copysignf(1.0f, theta) / (at + sqrtf(theta * theta + 1.0f));
-    const float c = 1.0f / sqrtf(t * t + 1.0f);
-    const float sn = t * c;
-    app = app - t * apq;
-    aqq = aqq + t * apq;
-    apq = 0.0f;
-    float x = arp, y = arq;
-    arp = c * x - sn * y;
-    arq = sn * x + c * y;
-    x = v0p; y = v0q; v0p = c * x - sn * y; v0q = sn * x + c * y;
-    x = v1p; y = v1q; v1p = c * x - sn * y; v1q = sn * x + c * y;
-    x = v2p; y = v2q; v2p = c * x - sn * y; v2q = sn * x + c * y;
+// Unit null vector of the symmetric 3x3 matrix with rows r0, r1, r2 (of
+// rank 2 up to rounding): the cross product of two rows is orthogonal to
+// both, and of the three pairs the one with the largest cross product is
+// the best conditioned.  A zero matrix gives e_z.
+__host__ __device__ __forceinline__ float3 cross3(float3 a, float3 b) {
+    return make_float3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+__host__ __device__ __forceinline__ float dot3(float3 a, float3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+
+__host__ __device__ __forceinline__ float3 null_vector(float3 r0, float3 r1, float3 r2) {
+    const float3 c01 = cross3(r0, r1), c02 = cross3(r0, r2), c12 = cross3(r1, r2);
+    const float d01 = dot3(c01, c01), d02 = dot3(c02, c02), d12 = dot3(c12, c12);
+    float3 c = c01;
+    float d = d01;
+    if (d02 > d) { c = c02; d = d02; }
+    if (d12 > d) { c = c12; d = d12; }
+    if (!(d > 0.0f)) return make_float3(0.0f, 0.0f, 1.0f);
+    const float inv = 1.0f / sqrtf(d);
+    return make_float3(c.x * inv, c.y * inv, c.z * inv);
 }
 
-// Unit eigenvector of the smallest eigenvalue of a symmetric 3x3 matrix, by
-// cyclic Jacobi sweeps in binary32 (pairs (0,1), (0,2), (1,2) in that order,
-// at most 8 sweeps, stopping once the off-diagonal mass is at rounding
-// level).  Its eigenvector error is ~ u ||C|| / (lambda2 - lambda3), the
-// perturbation bound itself.  The trigonometric closed form for 3x3
-// eigenvalues was tried first and dropped: in binary32 its acos step loses
-// accuracy to ~sqrt(u) when two eigenvalues nearly coincide (isotropic
-// planar patches), which the 1e-5 covariance bar exposes.  The matrix is
-// scaled by an exact power of two first; a zero matrix gives e_z.
+// Unit eigenvector of the smallest eigenvalue of a symmetric 3x3 matrix A,
+// in closed form, binary32.  The matrix is first scaled by an exact power
+// of two; a zero matrix gives e_z.
+//
+// Eigenvalues by the trigonometric form (Smith 1961): with m = tr(A)/3,
+// B = A - m I, p = sqrt(tr(B^2)/6) and r = det(B)/(2 p^3) in [-1, 1],
+// phi = acos(r)/3, the eigenvalues are m + 2p cos(phi + 2 pi j/3),
+// j = 0 (largest), 1 (smallest), 2.  Which one is computed decides the
+// accuracy (the hybrid of Kopp 2008, "Efficient numerical diagonalization
+// of hermitian 3x3 matrices"):
+// * r < 0: the middle eigenvalue is nearer the largest, so the smallest is
+//   the isolated one (lambda2 - lambda3 >= (lambda1 - lambda3)/2) and its
+//   value has a bounded derivative in r.  The normal is the null vector of
+//   A - lambda3 I.
+// * r >= 0: the two smallest are the close pair; the largest is isolated
+//   and accurate, its eigenvector e1 is the null vector of A - lambda1 I,
+//   and the normal is the smaller eigenvector of A restricted to the plane
+//   orthogonal to e1 (a 2x2 problem solved by one Jacobi rotation, exact
+//   for any separation of the pair, a repeated pair included).
+// Either way the normal's error is ~ u ||A|| / (lambda2 - lambda3), the
+// perturbation bound itself, as for an iterative solver.
 __host__ __device__ float3 min_eigvec(float a00, float a01, float a02, float a11, float a12, float a22) {
     const float amax = fmaxf(fmaxf(fabsf(a00), fabsf(a11)),
                              fmaxf(fabsf(a22), fmaxf(fmaxf(fabsf(a01), fabsf(a02)), fabsf(a12))));
@@ -349,23 +356,52 @@ __host__ __device__ float3 min_eigvec(float a00, float a01, float a02, float a11
     frexpf(amax, &e);
     const float sc = ldexpf(1.0f, -e);
     a00 *= sc; a01 *= sc; a02 *= sc; a11 *= sc; a12 *= sc; a22 *= sc;
-    float v00 = 1.0f, v01 = 0.0f, v02 = 0.0f;
-    float v10 = 0.0f, v11 = 1.0f, v12 = 0.0f;
-    float v20 = 0.0f, v21 = 0.0f, v22 = 1.0f;
-    for (int sweep = 0; sweep < 8; ++sweep) {
-        const float off = a01 * a01 + a02 * a02 + a12 * a12;
-        const float dia = a00 * a00 + a11 * a11 + a22 * a22;
-        if (!(off > 1e-15f * dia)) break;
-        jacobi_rotate(a00, a11, a01, a02, a12, v00, v01, v10, v11, v20, v21);  // (0,1), r = 2
-        jacobi_rotate(a00, a22, a02, a01, a12, v00, v02, v10, v12, v20, v22);  // (0,2), r = 1
-        jacobi_rotate(a11, a22, a12, a01, a02, v01, v02, v11, v12, v21, v22);  // (1,2), r = 0
+    const float m = (a00 + a11 + a22) / 3.0f;
+    const float b00 = a00 - m, b11 = a11 - m, b22 = a22 - m;
+    const float p2 = (b00 * b00 + b11 * b11 + b22 * b22 + 2.0f * (a01 * a01 + a02 * a02 + a12 * a12)) / 6.0f;
+    if (!(p2 > 0.0f)) return make_float3(0.0f, 0.0f, 1.0f);  // A = m I: every direction
+    const float p = sqrtf(p2);
+    const float det = b00 * (b11 * b22 - a12 * a12) - a01 * (a01 * b22 - a12 * a02) + a02 * (a01 * a12 - b11 * a02);
+    const float r = fminf(fmaxf(det / (2.0f * p2 * p), -1.0f), 1.0f);
+    const float phi = acosf(r) / 3.0f;
+    if (r < 0.0f) {
+        const float l3 = m + 2.0f * p * cosf(phi + 2.09439510f);
+        return null_vector(make_float3(a00 - l3, a01, a02), make_float3(a01, a11 - l3, a12),
+                           make_float3(a02, a12, a22 - l3));
     }
-    float3 n = make_float3(v00, v10, v20);
-    float lmin = a00;
-    if (a11 < lmin) { lmin = a11; n = make_float3(v01, v11, v21); }
-    if (a22 < lmin) { n = make_float3(v02, v12, v22); }
-    const float inv = 1.0f / sqrtf(n.x * n.x + n.y * n.y + n.z * n.z);
-    return make_float3(n.x * inv, n.y * inv, n.z * inv);
+    const float l1 = m + 2.0f * p * cosf(phi);
+    const float3 e1 = null_vector(make_float3(a00 - l1, a01, a02), make_float3(a01, a11 - l1, a12),
+                                  make_float3(a02, a12, a22 - l1));
+    // orthonormal u, v spanning the plane orthogonal to e1
+    const float ax = fabsf(e1.x), ay = fabsf(e1.y), az = fabsf(e1.z);
+    const float3 w = (ax <= ay && ax <= az) ? make_float3(1.0f, 0.0f, 0.0f)
+                   : (ay <= az ? make_float3(0.0f, 1.0f, 0.0f) : make_float3(0.0f, 0.0f, 1.0f));
+    float3 u = cross3(e1, w);
+    const float iu = 1.0f / sqrtf(dot3(u, u));
+    u = make_float3(u.x * iu, u.y * iu, u.z * iu);
+    const float3 v = cross3(e1, u);
+    const float3 Au = make_float3(a00 * u.x + a01 * u.y + a02 * u.z, a01 * u.x + a11 * u.y + a12 * u.z,
+                                  a02 * u.x + a12 * u.y + a22 * u.z);
+    const float3 Av = make_float3(a00 * v.x + a01 * v.y + a02 * v.z, a01 * v.x + a11 * v.y + a12 * v.z,
+                                  a02 * v.x + a12 * v.y + a22 * v.z);
+    const float suu = dot3(u, Au), suv = dot3(v, Au), svv = dot3(v, Av);
+    // the rotation (c, s) that diagonalises [[suu, suv], [suv, svv]] (the
+    // smaller root t of t^2 + 2 t theta - 1 = 0, Golub & Van Loan sec. 8.5):
+    // eigenvector (c, -s) for suu - t suv, (s, c) for svv + t suv
+    float c = 1.0f, sn = 0.0f, lu = suu, lv = svv;
+    if (suv != 0.0f) {
+        const float theta = (svv - suu) / (2.0f * suv);
+        const float at = fabsf(theta);
+        const float t = at > 1e18f ? 0.5f / theta : copysignf(1.0f, theta) / (at + sqrtf(theta * theta + 1.0f));
+        c = 1.0f / sqrtf(t * t + 1.0f);
+        sn = t * c;
+        lu = suu - t * suv;
+        lv = svv + t * suv;
+    }
+    const float x = lu <= lv ? c : sn, y = lu <= lv ? -sn : c;
+    const float3 nv = make_float3(x * u.x + y * v.x, x * u.y + y * v.y, x * u.z + y * v.z);
+    const float in = 1.0f / sqrtf(dot3(nv, nv));
+    return make_float3(nv.x * in, nv.y * in, nv.z * in);
 }
 
 // Covariance of one neighbourhood (Sec. III-C1, C_i of Eq. 19) from its
@@ -386,6 +422,22 @@ __device__ __forceinline__ void store6(float* out, float a, float b, float c, fl
     } else {
         out[0] = a; out[1] = b; out[2] = c; out[3] = d; out[4] = e; out[5] = f;
     }
+}
+
+// The end of every plain covariance: centred sums / k, then, for eps >= 0,
+// the plane regularisation C' = I - (1 - eps) n n^T; stored packed.
+__device__ __forceinline__ void cov_finish(float cxx, float cxy, float cxz, float cyy, float cyz, float czz,
+                                           float fk, float eps, float* out) {
+    cxx = cxx / fk; cxy = cxy / fk; cxz = cxz / fk;
+    cyy = cyy / fk; cyz = cyz / fk; czz = czz / fk;
+    if (eps < 0.0f) {
+        store6(out, cxx, cxy, cxz, cyy, cyz, czz);
+        return;
+    }
+    const float3 n = min_eigvec(cxx, cxy, cxz, cyy, cyz, czz);
+    const float f = 1.0f - eps;
+    store6(out, 1.0f - f * n.x * n.x, -f * n.x * n.y, -f * n.x * n.z, 1.0f - f * n.y * n.y, -f * n.y * n.z,
+           1.0f - f * n.z * n.z);
 }
 
 template <typename G>
@@ -413,16 +465,7 @@ __device__ __forceinline__ void cov_core(G&& get, int k, float eps, float* out) 
         cyz = __fmaf_rn(dy, dz, cyz);
         czz = __fmaf_rn(dz, dz, czz);
     }
-    cxx = cxx / fk; cxy = cxy / fk; cxz = cxz / fk;
-    cyy = cyy / fk; cyz = cyz / fk; czz = czz / fk;
-    if (eps < 0.0f) {
-        store6(out, cxx, cxy, cxz, cyy, cyz, czz);
-        return;
-    }
-    const float3 n = min_eigvec(cxx, cxy, cxz, cyy, cyz, czz);
-    const float f = 1.0f - eps;
-    store6(out, 1.0f - f * n.x * n.x, -f * n.x * n.y, -f * n.x * n.z, 1.0f - f * n.y * n.y, -f * n.y * n.z,
-           1.0f - f * n.z * n.z);
+    cov_finish(cxx, cxy, cxz, cyy, cyz, czz, fk, eps, out);
 }
 
 __device__ __forceinline__ void nan_row(float* out) {
@@ -578,6 +621,7 @@ struct TileArgs {
     float rho_scale;
     int last_first;  // issue tiles from the end of the query array
     CovKernel ck;    // kernel-descriptor weights; type 0: the plain covariance
+    float probe_c;   // > 0: each lane estimates its own starting radius (probe_radius)
 };
 
 // The covariance of a written row (caller or union indices; a leading -1
@@ -616,12 +660,15 @@ __device__ __forceinline__ void cas32(uint32_t& a, uint32_t& b) {
     b = hi;
 }
 
-// Batcher's odd-even merge sort over the first NN registers (NN a power of
-// two), ascending: merges sorted runs of length p into runs of 2p; within
-// a merge, elements k apart are compared, k halving from p, and only pairs
-// inside the same run of 2p.  The comparator list is computed at compile
-// time and expanded as a parameter pack, so every register index is a
-// constant (NN = 32: 191 comparators, where a bitonic network takes 240).
+// Batcher's odd-even merge sort over the first NN registers, ascending:
+// merges sorted runs of length p into runs of 2p; within a merge, elements
+// k apart are compared, k halving from p, and only pairs inside the same
+// run of 2p.  The comparator list is computed at compile time and expanded
+// as a parameter pack, so every register index is a constant (NN = 32: 191
+// comparators, where a bitonic network takes 240).  For NN not a power of
+// two the list is the next power of two's less every comparator that
+// reaches past NN: with the registers from NN on holding the largest key,
+// such a comparator never moves anything, so what remains sorts NN keys.
 template <int NN>
 struct OemNet {
     struct Table {
@@ -684,6 +731,29 @@ __device__ __forceinline__ u64 slot_key(const Grid& g, const Grid& dg, const uin
     return ((u64)__float_as_uint(d) << 32) | (u64)union_index<DEL>(g, tp, p);
 }
 
+// A lane's own starting radius where the map's density is uneven: the
+// points of the 27 cells around q (counted through the row index, no point
+// is read) set a surface density n / (9 h^2), and the radius of a disc
+// holding k points at that density, c h sqrt(k / n), is where the trial
+// radii start; at most 3 h (and 3 h when the block is empty).  Only the
+// search's speed depends on it.
+template <bool WIN>
+__device__ __forceinline__ float probe_radius(const Grid& g, float qx, float qy, float qz, int k, float c) {
+    const int cx = cell_of(qx, g.ox, g.inv_h), cy = cell_of(qy, g.oy, g.inv_h), cz = cell_of(qz, g.oz, g.inv_h);
+    const int x0 = max(cx - 1, WIN ? g.wlx : 0), x1 = min(cx + 1, WIN ? g.whx : g.dimx - 1);
+    const int y0 = max(cy - 1, WIN ? g.wly : 0), y1 = min(cy + 1, WIN ? g.why : g.dimy - 1);
+    const int z0 = max(cz - 1, WIN ? g.wlz : 0), z1 = min(cz + 1, WIN ? g.whz : g.dimz - 1);
+    uint32_t n = 0;
+    if (g.occ && x0 <= x1)
+        for (int z = z0; z <= z1; ++z)
+            for (int y = y0; y <= y1; ++y) {
+                const uint2 u = row_cell_ranks(g, y, z, x0, x1);
+                if (u.y > u.x) n += __ldg(&g.cell_start[u.y]) - __ldg(&g.cell_start[u.x]);
+            }
+    const float cap = 3.0f * g.h;
+    return n > 0 ? fminf(c * g.h * sqrtf((float)k / (float)n), cap) : cap;
+}
+
 // k <= 32: one query per lane.  Pass 1 counts, for each trial radius
 // r_j = m_j rho0, the target points with d2 <= t_j = min(r_j^2, tau), tau
 // certified for the box around the largest radius; the smallest t_j that
@@ -722,22 +792,24 @@ __device__ void lane_tile(const Grid& g, const Grid& dg, const float* __restrict
     bool fallback = false;
     int m = 0;
     float thr = -1.0f;
+    uint32_t visits = 0;  // candidate points whose distance this lane computed
     int lx = 0, hx = -1, ly = 0, hy = -1, lz = 0, hz = -1;
     float eta = 0.0f;
     int dlx = 0, dhx = -1, dly = 0, dhy = -1, dlz = 0, dhz = -1;
     float deta = 0.0f;
-    // Up to two lane-parallel attempts: a lane whose largest trial radius
+    // Up to three lane-parallel attempts: a lane whose largest trial radius
     // held fewer than k points retries with the radii x1.8.  A lane whose
     // count jumped from below k at one radius to above CAP at the next (a
     // wall entering the ball between two rungs) retries with thresholds
     // spaced evenly in d2 between those two radii, where a surface's count
     // grows evenly; one whose smallest radius held more than CAP retries
     // with the radii x0.7.  Only lanes that still fail go to the warp
-    // search.
-    float rho = rho0;
+    // search, whose latency (tens of microseconds for one query) would
+    // otherwise set the end of the launch.
+    float rho = finite && a.probe_c > 0.0f ? probe_radius<WIN>(g, qx, qy, qz, a.k, a.probe_c) : rho0;
     float rlo2 = 0.0f, rhi2 = -1.0f;  // the interval to subdivide (squared radii), rhi2 > 0
     bool todo = finite;
-    for (int attempt = 0; attempt < 2 && __any_sync(FULL, todo); ++attempt) {
+    for (int attempt = 0; attempt < 3 && __any_sync(FULL, todo); ++attempt) {
         if (todo) {
             todo = false;
             const bool refine = rhi2 > 0.0f;
@@ -795,6 +867,7 @@ __device__ void lane_tile(const Grid& g, const Grid& dg, const float* __restrict
                 }
                 auto count = [&](uint32_t, const float4 p) {
                     const float d = sqdist_pinned(qx, qy, qz, p.x, p.y, p.z);
+                    ++visits;
 #pragma unroll
                     for (int j = 0; j < NRAD; ++j) c[j] += d <= t[j] ? 1 : 0;
                 };
@@ -820,19 +893,16 @@ __device__ void lane_tile(const Grid& g, const Grid& dg, const float* __restrict
                 }
                 if (js < 0 || cj > CAP) {
                     fallback = true;
-                    // too few within the certified radii: widen; too many: subdivide
-                    // the jump or narrow (unless the certified radius, not the trial
-                    // radius, was short)
+                    // too few within the certified radii: widen (a wider box also
+                    // certifies further); too many: subdivide the jump or narrow
                     const bool widen = js < 0;
-                    if (!(widen && t[NRAD - 1] >= tau)) {
-                        todo = true;
-                        if (!widen && js > 0 && !refine) {
-                            rlo2 = tl;
-                            rhi2 = tj;
-                        } else {
-                            rho = widen ? rho * 1.8f : rho * 0.7f;
-                            rhi2 = -1.0f;
-                        }
+                    todo = true;
+                    if (!widen && js > 0 && !refine) {
+                        rlo2 = tl;
+                        rhi2 = tj;
+                    } else {
+                        rho = widen ? rho * 1.8f : rho * 0.7f;
+                        rhi2 = -1.0f;
                     }
                 } else {
                     m = cj;
@@ -845,6 +915,7 @@ __device__ void lane_tile(const Grid& g, const Grid& dg, const float* __restrict
         int w = 0;
         auto collect = [&](uint32_t pos, const float4 p) {
             const float d = sqdist_pinned(qx, qy, qz, p.x, p.y, p.z);
+            ++visits;
             if (d <= thr && w < CAP) {
                 posl[w * 32 + lane] = pos;
                 ++w;
@@ -954,9 +1025,11 @@ __device__ void lane_tile(const Grid& g, const Grid& dg, const float* __restrict
         atomicOr(g.status, ST_NONFINITE);
     }
     unsigned fb = __ballot_sync(FULL, fallback);
+    const unsigned nvis = __reduce_add_sync(FULL, visits);
     if (lane == 0) {
         atomicAdd(&g.stats[0], (unsigned long long)cnt);
         if (fb) atomicAdd(&g.stats[1], (unsigned long long)__popc(fb));
+        if (nvis) atomicAdd(&g.stats[3], (unsigned long long)nvis);
     }
     while (fb) {
         const int f = __ffs(fb) - 1;

@@ -69,6 +69,7 @@ void default_tune(pc_tune* tu) {
     tu->warps = 4;
     tu->rho_scale = 0.9f;
     tu->order = 0;
+    tu->probe = 0;
 }
 
 pc_status read_and_clear_status(pc_target_s* t, cudaStream_t s) {
@@ -127,6 +128,13 @@ pc_status calibrate_rho(pc_target_s* t, cudaStream_t s) {
         const size_t pos = (col.size() * 3) / 4;
         std::nth_element(col.begin(), col.begin() + pos, col.end());
         t->rho_hint[kk] = col[pos];
+        // spread of the distances at k = min(kc, 16): a map whose density
+        // varies widely (a p90 / p25 above 1.55) gets per-query starting radii
+        if (kk == std::min(kc, 16) - 1) {
+            std::sort(col.begin(), col.end());
+            const float p25 = col[col.size() / 4], p90 = col[(col.size() * 9) / 10];
+            t->uneven = p25 > 0.0f && p90 > 1.55f * p25 ? 1 : 0;
+        }
     }
     return PC_OK;
 }
@@ -168,7 +176,10 @@ static pc_status build_target_internal(const float* xyz, int64_t M, const pc_bui
     if (like) ob.cell_size = like->g.h;
     pc_status r = pc_build_grid(xyz, M, ob, st, t);
     if (r == PC_OK) {
-        if (like) std::memcpy(t->rho_hint, like->rho_hint, sizeof(t->rho_hint));
+        if (like) {
+            std::memcpy(t->rho_hint, like->rho_hint, sizeof(t->rho_hint));
+            t->uneven = like->uneven;
+        }
         else r = calibrate_rho(t, st);
     }
     if (r != PC_OK) {
@@ -210,6 +221,11 @@ pc_status pc_from_cuda(cudaError_t e) {
 bool pc_target_is_live(const pc_target_s* t) { return t != nullptr && live(t); }
 
 bool pc_is_device_ptr(const void* p) { return is_device_ptr(p); }
+
+float pc_probe_c(const pc_target_s* t) {
+    const int p = t->tune.probe;
+    return (p == 2 || (p == 0 && t->uneven)) ? 1.6f : 0.0f;
+}
 
 float pc_rho0(const pc_target_s* t, int k) {
     float r = (k >= 1 && k <= 64) ? t->rho_hint[k - 1] : 0.0f;
@@ -267,7 +283,7 @@ pc_status pc_set_tune(pc_target t, const pc_tune* tune) {
         return PC_OK;
     }
     if (tune->tile > 32 || tune->warps > 8 || !(std::isfinite(tune->rho_scale)) || tune->order < 0 ||
-        tune->order > 1)
+        tune->order > 1 || tune->probe < 0 || tune->probe > 2)
         return PC_ERR_INVALID_ARG;
     t->tune = *tune;
     if (t->tune.tile <= 0) t->tune.tile = 32;

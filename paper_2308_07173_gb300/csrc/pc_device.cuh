@@ -99,9 +99,10 @@ __device__ __forceinline__ uint2 lookup_cell(const Grid& g, unsigned long long k
     return make_uint2(0u, 0u);
 }
 
-// Points of the occupied cells x0..x1 (x0 <= x1) of row (cy, cz) as one
-// range (start, count) of pts, through the row index.
-__device__ __forceinline__ uint2 row_range(const Grid& g, int cy, int cz, int x0, int x1) {
+// Ranks (u0, u1) of the occupied cells x0..x1 (x0 <= x1) of row (cy, cz)
+// among all occupied cells, through the row index: the row's points are
+// pts[cell_start[u0], cell_start[u1]).
+__device__ __forceinline__ uint2 row_cell_ranks(const Grid& g, int cy, int cz, int x0, int x1) {
     const int64_t base = (int64_t)g.dimx * ((int64_t)cy + (int64_t)g.dimy * cz);
     const int64_t L0 = base + x0, L1 = base + x1;
     const int64_t w0 = L0 >> 5, w1 = L1 >> 5;
@@ -112,9 +113,16 @@ __device__ __forceinline__ uint2 row_range(const Grid& g, int cy, int cz, int x0
     const uint32_t upto = b1 == 31u ? 0xffffffffu : ((2u << b1) - 1u);
     const uint32_t u1 = (w1 == w0) ? r0 + __popc(o0 & upto)
                                    : __ldg(&g.rank[w1]) + __popc(__ldg(&g.occ[w1]) & upto);
-    if (u1 == u0) return make_uint2(0u, 0u);
-    const uint32_t s = __ldg(&g.cell_start[u0]);
-    return make_uint2(s, __ldg(&g.cell_start[u1]) - s);
+    return make_uint2(u0, u1);
+}
+
+// Points of the occupied cells x0..x1 (x0 <= x1) of row (cy, cz) as one
+// range (start, count) of pts, through the row index.
+__device__ __forceinline__ uint2 row_range(const Grid& g, int cy, int cz, int x0, int x1) {
+    const uint2 u = row_cell_ranks(g, cy, cz, x0, x1);
+    if (u.y == u.x) return make_uint2(0u, 0u);
+    const uint32_t s = __ldg(&g.cell_start[u.x]);
+    return make_uint2(s, __ldg(&g.cell_start[u.y]) - s);
 }
 
 // The pinned binary32 squared distance: fmaf(dz,dz, fmaf(dy,dy, dx*dx)).

@@ -39,6 +39,7 @@ struct pc_target_s {
     pc_tune tune;
     float bbox_max[3];
     float rho_hint[64];
+    int uneven;  // the calibration's k-th-neighbour distances spread widely (p90 / p25 > 1.55)
     int64_t table_cap;
     int64_t device_bytes;
     // owned device memory
@@ -152,6 +153,8 @@ cudaError_t pc_launch_pack_xyz(const pc_target_s* t, float* out, cudaStream_t s)
 
 // pc_api.cu
 float pc_rho0(const pc_target_s* t, int k);
+// The probe constant of the lane path's per-query starting radius (0: off).
+float pc_probe_c(const pc_target_s* t);
 // Launch shape of a batched call over caller-provided scans.
 struct BatchShape {
     int64_t tiles;  // work items (tiles of `tile` queries) over all scans; 0: nothing to do

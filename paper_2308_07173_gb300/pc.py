@@ -92,7 +92,7 @@ class pc_window(ctypes.Structure):
 
 class pc_tune(ctypes.Structure):
     _fields_ = [("tile", ctypes.c_int), ("warps", ctypes.c_int), ("rho_scale", ctypes.c_float),
-                ("order", ctypes.c_int)]
+                ("order", ctypes.c_int), ("probe", ctypes.c_int)]
 
 
 class pc_target_info(ctypes.Structure):
@@ -381,8 +381,8 @@ class Target:
             "delta_m": i.delta_m,
         }
 
-    def set_tune(self, tile: int = 0, warps: int = 0, rho_scale: float = 0.0, order: int = 0):
-        pc_set_tune(self.handle, pc_tune(tile, warps, rho_scale, order))
+    def set_tune(self, tile: int = 0, warps: int = 0, rho_scale: float = 0.0, order: int = 0, probe: int = 0):
+        pc_set_tune(self.handle, pc_tune(tile, warps, rho_scale, order, probe))
 
     def knn(self, q, k: int, idx=None, d2=None, stream=None):
         torch = _torch()
