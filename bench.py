@@ -24,6 +24,7 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -41,6 +42,8 @@ EPS = 1e-3
 MAP_POINTS = 2_000_000
 FLUSH_BYTES = 256 << 20  # > 129 MB L2
 FALLBACK_HBM_GBS = 6800.0
+TIMED_DEVICE_MS = 1200.0  # device time the C2 timed region aims for
+SEARCH_KERNEL = "k_knn<0,1,0> (fused search + covariance, whole-map variant)"
 KERNEL_SOURCES = ["paper_2308_07173_gb300/csrc/knn_kernels.cuh", "paper_2308_07173_gb300/csrc/pc_device.cuh",
                   "paper_2308_07173_gb300/csrc/pc_search.cuh"]
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "knn_cov_c2_ncu.json")
@@ -85,6 +88,24 @@ def measured_traffic():
         return float(d["dram_bytes_per_launch_full_size"]) if d else None
     except (KeyError, TypeError, ValueError):
         return None
+
+
+def l2_figures(ms_per_launch):
+    """L2 traffic of the search kernel from the committed capture (lts__t_bytes
+    per launch, valid while the kernel source is unchanged) over the measured
+    launch time, beside its DRAM bytes."""
+    d = measured_profile()
+    if not d or "l2_bytes_per_launch" not in d:
+        return None
+    l2b = float(d["l2_bytes_per_launch"])
+    out = {"l2_bytes_per_launch": l2b, "achieved_l2_gbs": l2b / (ms_per_launch / 1e3) / 1e9,
+           "dram_bytes_per_launch": d.get("dram_bytes_per_launch_full_size"),
+           "source": "lts__t_bytes.sum and dram__bytes of the committed ncu capture "
+                     "(profiles/knn_cov_c2_ncu.json), over this run's launch time"}
+    if "candidates_per_query" in d:
+        out["candidates_per_query"] = d["candidates_per_query"]
+        out["candidate_bytes_per_launch"] = d.get("candidate_bytes_per_launch")
+    return out
 
 
 def issue_roofline(ms_per_launch, clk, sms):
@@ -248,7 +269,14 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4", "c5", "gicp", "window", "kernel", "wall", "append"],
                     help="c2 is the headline; the others print their own line")
-    ap.add_argument("--duration", type=float, default=3.0, help="c4: seconds of arrivals")
+    ap.add_argument("--duration", type=float, default=10.0, help="c4: seconds of arrivals")
+    ap.add_argument("--lambdas", default="0.5,1,2,4", help="c4: arrival-rate multiples swept")
+    ap.add_argument("--served-duration", type=float, default=2.0,
+                    help="seconds of arrivals in the C2 line's served sub-object")
+    ap.add_argument("--scans-per-step", type=int, default=0,
+                    help="c2: scans per timed step (0: enough for about a second of device time)")
+    ap.add_argument("--headline-only", action="store_true",
+                    help="c2: skip the batched and served sub-objects")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -261,8 +289,29 @@ def main():
     return run_c2(args)
 
 
+def algorithmic_roofline(md, info, idx_list, n_queries: int, k: int, ms: float) -> dict:
+    """HBM roofline of one search launch: algorithmic bytes N (12 + 8k + 24)
+    + 12 U_p + 8 U_c (U_p distinct target points in the answers, U_c the
+    distinct cells holding them) over the launch time, against the measured
+    copy bandwidth."""
+    import torch
+
+    ui = torch.unique(torch.cat([i.reshape(-1) for i in idx_list]).long())
+    ui = ui[ui >= 0]
+    U_p = int(ui.numel())
+    pts = md[ui]
+    o = torch.tensor(info["origin"], device=md.device)
+    cells = torch.floor((pts - o) * (1.0 / info["cell_size"])).long()
+    ckey = (cells[:, 0] << 42) | (cells[:, 1] << 21) | cells[:, 2]
+    U_c = int(torch.unique(ckey).numel())
+    alg = n_queries * (12 + 8 * k + 24) + 12 * U_p + 8 * U_c
+    peak, kind = peaks()
+    achieved = alg / (ms / 1e3) / 1e9
+    return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "peak_source": kind, "algorithmic_bytes": alg, "U_p": U_p, "U_c": U_c}
+
+
 def run_c2(args):
-    import numpy as np
     import torch
 
     from paper_2308_07173_gb300 import pc, sharding
@@ -283,7 +332,8 @@ def run_c2(args):
     N = len(q)
     dev = torch.device("cuda", local)
     stream = torch.cuda.Stream(dev)
-    t = pc.Target(torch.from_numpy(m).to(dev))
+    md = torch.from_numpy(m).to(dev)
+    t = pc.Target(md)
     info = t.info()
     qd = torch.from_numpy(q).to(dev)
     idx = torch.empty((N, K_NN), dtype=torch.int32, device=dev)
@@ -292,28 +342,43 @@ def run_c2(args):
     flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
     torch.cuda.synchronize()
 
-    def step():
+    def scan():
         t.knn_cov(qd, K_NN, EPS, idx, d2, cov, stream=stream)
 
+    warm = []
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
             flush.fill_(1)
-            step()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            scan()
+            b.record(stream)
+            warm.append((a, b))
     stream.synchronize()
     assert t.sync_status(stream) == pc.PC_OK
+    # A step is R scans back to back, each after an L2 flush, so that the
+    # timed region holds about a second of device time whatever --steps is
+    # (enough for the clock samples); every scan is timed by its own events.
+    est = statistics.median(a.elapsed_time(b) for a, b in warm)
+    R = args.scans_per_step or max(1, min(4000, int(math.ceil(TIMED_DEVICE_MS / (args.steps * est)))))
+    if dist:
+        R = int(sharding.reduce_max(R, dev))
+    t.stats(reset=True, stream=stream)
 
     clocks = Clocks(local)
     clocks.start()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    ev = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(R)]
+          for _ in range(args.steps)]
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
     with torch.cuda.stream(stream):
         for i in range(args.steps):
-            flush.fill_(1)
-            ev[i][0].record(stream)
-            step()
-            ev[i][1].record(stream)
+            for r in range(R):
+                flush.fill_(1)
+                ev[i][r][0].record(stream)
+                scan()
+                ev[i][r][1].record(stream)
     stream.synchronize()
     torch.cuda.synchronize()
     if dist:
@@ -322,26 +387,19 @@ def run_c2(args):
     st = t.sync_status(stream)
     assert st == pc.PC_OK, pc.pc_status_string(st)
     path_stats = t.stats(reset=True, stream=stream)
-    ms = [a.elapsed_time(b) for a, b in ev]
-    total_ms = sum(ms)
+    scan_ms = [a.elapsed_time(b) for step in ev for a, b in step]
+    total_ms = sum(scan_ms)
     total_ms = sharding.reduce_max(total_ms, dev)
     n_all = sharding.reduce_sum(N, dev)
-    value = n_all * args.steps / (total_ms / 1e3)
+    value = n_all * R * args.steps / (total_ms / 1e3)
     ms_per_step = total_ms / args.steps
-    lat = sorted(ms)
+    ms_per_scan = total_ms / (args.steps * R)
+    lat = sorted(scan_ms)
 
-    # roofline of the search kernel: algorithmic bytes per launch
-    ui = torch.unique(idx.view(-1).long())
-    U_p = int(ui.numel())
-    pts = torch.from_numpy(m).to(dev)[ui]
-    o = torch.tensor(info["origin"], device=dev)
-    cells = torch.floor((pts - o) * (1.0 / info["cell_size"])).long()
-    ckey = (cells[:, 0] << 42) | (cells[:, 1] << 21) | cells[:, 2]
-    U_c = int(torch.unique(ckey).numel())
-    alg_bytes = N * (12 + 8 * K_NN + 24) + 12 * U_p + 8 * U_c
-    peak, peak_kind = peaks()
-    achieved = alg_bytes / (ms_per_step / 1e3) / 1e9
-    traffic = measured_traffic()
+    roof = algorithmic_roofline(md, info, [idx], N, K_NN, ms_per_scan)
+    roof["traffic"] = measured_traffic()
+    roof["kernel"] = SEARCH_KERNEL
+    l2 = l2_figures(ms_per_scan)
 
     # end to end through the host-buffer entry
     qh = torch.from_numpy(q).pin_memory()
@@ -364,6 +422,14 @@ def run_c2(args):
     e2e_value = n_all * len(e2e_t) / e2e_total
     assert torch.equal(outs[0], idx.cpu())
 
+    extras = {}
+    if rank == 0 and ws == 1 and not args.headline_only:
+        t.close()
+        t = None
+        extras["batched"] = measure_c3(md, m, reps=10)
+        extras["served"] = measure_c4(duration=args.served_duration, speeds=(("nominal", 1.0),
+                                                                             ("saturated", 1e6)))
+
     base = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         base = cpu_baseline(q, m)
@@ -375,28 +441,30 @@ def run_c2(args):
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "c2_scan131k_vs_map2M_k20_eps1e-3", "n_queries": N, "map_points": MAP_POINTS,
                        "k": K_NN, "eps": EPS, "cell_size": info["cell_size"], "occupied_cells": info["ncells"],
-                       "l2": "flushed by a 256 MB write before every timed step (outside the events)",
+                       "scans_per_step": R, "ms_per_scan": ms_per_scan,
+                       "l2": "flushed by a 256 MB write before every scan (outside the scan's events)",
                        "parallelism": f"queries sharded by scan, {ws} rank(s), no collective"},
             "latency_ms": {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
-                           "max": lat[-1]},
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": traffic, "peak_source": peak_kind,
-                         "algorithmic_bytes": alg_bytes, "U_p": U_p, "U_c": U_c,
-                         "kernel": "k_knn<0,1,0> (fused search + covariance, whole-map variant)"},
+                           "max": lat[-1], "scans": len(lat)},
+            "roofline": roof,
+            "l2_traffic": l2,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 12 * N,
-                    "d2h_bytes_per_step": N * (8 * K_NN + 24)},
-            "issue_roofline": issue_roofline(ms_per_step, clk,
+                    "d2h_bytes_per_step": N * (8 * K_NN + 24), "step": "one scan through pc_knn_cov_host"},
+            "issue_roofline": issue_roofline(ms_per_scan, clk,
                                              torch.cuda.get_device_properties(dev).multi_processor_count),
             "clocks": clk,
             "search_paths": {"queries": path_stats["queries"],
                              "warp_search_frac": path_stats["warp_search"] / max(1, path_stats["queries"]),
-                             "exhaustive": path_stats["exhaustive"]},
-            "gpu_launches": args.steps,
+                             "exhaustive": path_stats["exhaustive"],
+                             "candidates_per_query": path_stats.get("candidates", 0) / max(1, path_stats["queries"])},
+            "gpu_launches": args.steps * R,
         }
+        line.update(extras)
         if base is not None:
             line["cpu_baseline"] = base
         print(json.dumps(line), flush=True)
-    t.close()
+    if t is not None:
+        t.close()
     if dist:
         dist.destroy_process_group()
     return 0
@@ -451,25 +519,24 @@ def run_c1(args):
     return 0
 
 
-def run_c3(args):
-    """64 scans of 20k-130k points against the 2M map: one batched launch
-    (a warp per scan tile) replayed as a CUDA graph vs 64 sequential
-    launches."""
+def measure_c3(md, m, reps: int = 10, tuned: dict = None) -> dict:
+    """64 scans of 20k-130k points against the 2M map: one batched launch (a
+    warp per scan tile) replayed as a CUDA graph vs 64 sequential launches,
+    with identical results asserted.  Uses the tuner's cached configuration
+    for this map and batch when one exists, else the defaults."""
     import torch
 
     from paper_2308_07173_gb300 import autotune, pc
     from paper_2308_07173_gb300 import workloads as W
 
-    pc.load()
-    _, m = W.scan_vs_map(MAP_POINTS)
     scans = W.scan_batch(64, seed=4)
-    md = torch.from_numpy(m).cuda()
     dev = md.device
     qs = [torch.from_numpy(x).to(dev) for x in scans]
-    sample = torch.cat(qs[:6])
-    tuned = autotune.tune(md, sample, K_NN, EPS, occupancies=(8, 12, 16), rho_scales=(0.85, 0.9, 1.0),
-                          warps=(2, 4), reps=8)["best"]
-    t = autotune.apply(md, tuned)
+    npts = sum(len(q) for q in qs)
+    if tuned is None:
+        tuned = autotune.lookup(autotune.default_cache(), K_NN, md.shape[0], npts)
+    t = autotune.apply(md, tuned) if tuned else pc.Target(md)
+    info = t.info()
     bufs = [(q, torch.empty((len(q), K_NN), dtype=torch.int32, device=dev),
              torch.empty((len(q), K_NN), dtype=torch.float32, device=dev),
              torch.empty((len(q), 6), dtype=torch.float32, device=dev)) for q in qs]
@@ -482,52 +549,98 @@ def run_c3(args):
             t.knn_cov(q, K_NN, EPS, i, d, c, stream=s)
 
     b = pc.Batch(t, bufs, K_NN, EPS)
-    reps = min(args.steps, 50)
+    clocks = Clocks(dev.index or 0)
+    clocks.start()
     ms_seq, _ = _timed(sequential, flush, reps, s)
-    ms_bat, _ = _timed(lambda: b.run(s), flush, reps, s)
-    same = all(torch.equal(x[1], y[0]) and torch.equal(x[3].view(torch.int32), y[2].view(torch.int32))
-               for x, y in zip(bufs, seq_out))
+    ms_bat, v_bat = _timed(lambda: b.run(s), flush, reps, s)
+    clk = clocks.stop()
+    same = all(torch.equal(x[1], y[0]) and torch.equal(x[2].view(torch.int32), y[1].view(torch.int32))
+               and torch.equal(x[3].view(torch.int32), y[2].view(torch.int32)) for x, y in zip(bufs, seq_out))
     assert same, "batched results differ from sequential"
-    npts = sum(len(q) for q in qs)
-    _line("query points/sec, 64-scan batch (20k-130k each) vs 2M map, kNN(k=20)+cov", npts / (ms_bat / 1e3),
-          UNIT, ms_bat, args, {"workload": "c3_64scans_logu20k-130k_map2M_k20", "queries": npts,
-                               "tuned": tuned, "form": "one launch over the scans' tile table, CUDA graph replay"},
-          sequential={"value": npts / (ms_seq / 1e3), "ms": ms_seq, "launches": 64},
-          speedup_vs_sequential=ms_seq / ms_bat, identical_to_sequential=bool(same), gpu_launches=1)
-    return 0
+    roof = algorithmic_roofline(md, info, [x[1] for x in bufs], npts, K_NN, ms_bat)
+    b.close()
+    t.close()
+    return {"workload": "c3_64scans_logu20k-130k_map2M_k20", "queries": npts, "value": npts / (ms_bat / 1e3),
+            "unit": UNIT, "ms": ms_bat, "ms_p99": v_bat[min(len(v_bat) - 1, int(0.99 * len(v_bat)))],
+            "form": "one launch over the scans' tile table, CUDA graph replay",
+            "tuned": tuned or "defaults (no cached configuration)",
+            "sequential": {"value": npts / (ms_seq / 1e3), "ms": ms_seq, "launches": 64},
+            "speedup_vs_sequential": ms_seq / ms_bat, "identical_to_sequential": bool(same),
+            "roofline": roof, "clocks": clk, "gpu_launches_per_step": 1}
 
 
-def run_c4(args):
-    """Serving: Poisson scans from 8 vehicles x 3 LiDARs at 20 Hz against a
-    resident 5M-point map; continuous batching vs one call per scan."""
+def run_c3(args):
     import torch
 
-    from paper_2308_07173_gb300 import pc, serve
+    from paper_2308_07173_gb300 import pc
     from paper_2308_07173_gb300 import workloads as W
 
     pc.load()
-    tr = W.oval_1500()
-    m = tr.sample_map(5_000_000, seed=5)
+    _, m = W.scan_vs_map(MAP_POINTS)
     md = torch.from_numpy(m).cuda()
-    t = pc.Target(md)
-    arr = W.arrival_stream(duration=args.duration, seed=5)
+    r = measure_c3(md, m, reps=min(args.steps, 50))
+    _line("query points/sec, 64-scan batch (20k-130k each) vs 2M map, kNN(k=20)+cov", r.pop("value"),
+          r.pop("unit"), r["ms"], args, {"workload": r.pop("workload"), "queries": r["queries"]},
+          **r, gpu_launches=1)
+    return 0
+
+
+def measure_c4(duration: float, speeds, map_points: int = 5_000_000, warm_scans: int = 20) -> dict:
+    """Serving: Poisson scans from 8 vehicles x 3 LiDARs at 20 Hz (replayed
+    `speed` times faster: the arrival rate scales by `speed`) against a
+    resident map; continuous batching vs one host-buffer call per scan."""
+    import torch
+
+    from paper_2308_07173_gb300 import autotune, pc, serve
+    from paper_2308_07173_gb300 import workloads as W
+
+    tr = W.oval_1500()
+    m = tr.sample_map(map_points, seed=5)
+    md = torch.from_numpy(m).cuda()
+    arr = W.arrival_stream(duration=duration, seed=5)
     reqs = serve.requests_from_arrivals(arr)
+    npts = sum(r.n for r in reqs)
+    tuned = autotune.lookup(autotune.default_cache(), K_NN, map_points, 0)
+    t = autotune.apply(md, tuned) if tuned else pc.Target(md)
     serve.prepare(reqs)
     srv = serve.Server(t, K_NN, EPS, hbm_budget=2 << 30, max_step_scans=16, slots=3)
-    warm = serve.requests_from_arrivals(arr[:20])
+    warm = serve.requests_from_arrivals(arr[:warm_scans])
     serve.prepare(warm)
     srv.serve(warm, speed=1e6)
     serve.serve_per_scan(t, K_NN, EPS, warm, speed=1e6)
-    out = {}
-    for name, speed in (("nominal", 1.0), ("saturated", 1e6)):
-        out[f"served_{name}"] = srv.serve(reqs, speed=speed)
-        out[f"per_scan_{name}"] = serve.serve_per_scan(t, K_NN, EPS, reqs, speed=speed)
-    sat = out["served_saturated"]
+    out = {"workload": f"c4_24lidars_20hz_poisson_map{map_points // 1_000_000}M_k20",
+           "arrival_seconds": duration, "scans": len(reqs), "points": npts,
+           "offered_points_per_s_at_1x": npts / duration, "hbm_budget_bytes": 2 << 30,
+           "max_step_scans": 16, "slots": 3, "tuned": tuned or "defaults (no cached configuration)"}
+    for name, speed in speeds:
+        clocks = Clocks(torch.cuda.current_device())
+        clocks.start()
+        sv = srv.serve(reqs, speed=speed)
+        ps = serve.serve_per_scan(t, K_NN, EPS, reqs, speed=speed)
+        clk = clocks.stop()
+        out[name] = {"arrival_rate_multiple": speed if speed < 1e5 else "all at t=0",
+                     "served": sv, "per_scan": ps, "clocks": clk,
+                     "served_p99_over_per_scan": sv["p99_ms"] / ps["p99_ms"],
+                     "served_throughput_over_per_scan": sv["throughput_pts_s"] / ps["throughput_pts_s"]}
+    assert t.sync_status() == pc.PC_OK
+    t.close()
+    return out
+
+
+def run_c4(args):
+    """C4 with the arrival-rate sweep: 10 s of arrivals replayed at
+    --lambdas multiples of the nominal 480 scans/s, plus all at once
+    (saturated), served vs per-scan at each rate."""
+    from paper_2308_07173_gb300 import pc
+
+    pc.load()
+    lams = [float(x) for x in args.lambdas.split(",") if x]
+    speeds = [(f"x{l:g}", l) for l in lams] + [("saturated", 1e6)]
+    r = measure_c4(args.duration, speeds)
+    sat = r["saturated"]["served"]
     _line("sustained points/sec and p50/p99 scan latency, 24 LiDARs x 20 Hz vs resident 5M map, kNN(k=20)+cov",
           sat["throughput_pts_s"], UNIT, 1e3 * sat["wall_s"] / max(1, sat["steps"]), args,
-          {"workload": "c4_24lidars_20hz_poisson_map5M_k20", "arrival_seconds": args.duration,
-           "scans": len(reqs), "hbm_budget_bytes": 2 << 30, "max_step_scans": 16, "slots": 3},
-          serving=out)
+          {"workload": r["workload"], "arrival_seconds": args.duration, "scans": r["scans"]}, serving=r)
     return 0
 
 
