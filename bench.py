@@ -311,6 +311,40 @@ def algorithmic_roofline(md, info, idx_list, n_queries: int, k: int, ms: float) 
             "peak_source": kind, "algorithmic_bytes": alg, "U_p": U_p, "U_c": U_c}
 
 
+def copy_bandwidth(dev, stream, qh, qd, outs, douts) -> dict:
+    """Where the end-to-end time goes: the host-to-device upload of one scan
+    and the device-to-host download of its three outputs, each timed alone
+    with CUDA events on the bench stream (pinned host buffers, as the host
+    entry uses), next to plain device-to-pinned-host copies of 1-64 MB."""
+    import torch
+
+    def timed(fn, reps=20):
+        for _ in range(3):
+            fn()
+        ts = []
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            b.synchronize()
+            ts.append(a.elapsed_time(b))
+        return statistics.median(ts)
+
+    with torch.cuda.stream(stream):
+        up = timed(lambda: qd.copy_(qh, non_blocking=True))
+        down = timed(lambda: [h.copy_(d, non_blocking=True) for h, d in zip(outs, douts)])
+        out = {"upload_ms": up, "upload_gbs": qh.numel() * 4 / up / 1e6,
+               "download_ms": down, "download_gbs": sum(h.numel() * 4 for h in outs) / down / 1e6,
+               "d2h_pinned_gbs": {}}
+        for mb in (1, 4, 16, 24, 64):
+            src = torch.empty(mb << 20, dtype=torch.uint8, device=dev)
+            dst = torch.empty(mb << 20, dtype=torch.uint8, pin_memory=True)
+            ms = timed(lambda: dst.copy_(src, non_blocking=True))
+            out["d2h_pinned_gbs"][f"{mb}MB"] = (mb << 20) / ms / 1e6
+    return out
+
+
 def run_c2(args):
     import torch
 
@@ -333,7 +367,10 @@ def run_c2(args):
     dev = torch.device("cuda", local)
     stream = torch.cuda.Stream(dev)
     md = torch.from_numpy(m).to(dev)
-    t = pc.Target(md)
+    from paper_2308_07173_gb300 import autotune
+
+    tuned = autotune.lookup(autotune.default_cache(), K_NN, MAP_POINTS, N)
+    t = autotune.apply(md, tuned) if tuned else pc.Target(md)
     info = t.info()
     qd = torch.from_numpy(q).to(dev)
     idx = torch.empty((N, K_NN), dtype=torch.int32, device=dev)
@@ -421,6 +458,7 @@ def run_c2(args):
     e2e_total = sharding.reduce_max(e2e_total, dev)
     e2e_value = n_all * len(e2e_t) / e2e_total
     assert torch.equal(outs[0], idx.cpu())
+    copy_probe = copy_bandwidth(dev, stream, qh, qd, outs, (idx, d2, cov)) if rank == 0 else None
 
     extras = {}
     if rank == 0 and ws == 1 and not args.headline_only:
@@ -442,6 +480,7 @@ def run_c2(args):
             "config": {"workload": "c2_scan131k_vs_map2M_k20_eps1e-3", "n_queries": N, "map_points": MAP_POINTS,
                        "k": K_NN, "eps": EPS, "cell_size": info["cell_size"], "occupied_cells": info["ncells"],
                        "scans_per_step": R, "ms_per_scan": ms_per_scan,
+                       "tuned": tuned or "defaults (no cached configuration)",
                        "l2": "flushed by a 256 MB write before every scan (outside the scan's events)",
                        "parallelism": f"queries sharded by scan, {ws} rank(s), no collective"},
             "latency_ms": {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
@@ -449,7 +488,8 @@ def run_c2(args):
             "roofline": roof,
             "l2_traffic": l2,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 12 * N,
-                    "d2h_bytes_per_step": N * (8 * K_NN + 24), "step": "one scan through pc_knn_cov_host"},
+                    "d2h_bytes_per_step": N * (8 * K_NN + 24), "step": "one scan through pc_knn_cov_host",
+                    "copies": copy_probe},
             "issue_roofline": issue_roofline(ms_per_scan, clk,
                                              torch.cuda.get_device_properties(dev).multi_processor_count),
             "clocks": clk,
@@ -652,33 +692,48 @@ def run_c5(args):
     from paper_2308_07173_gb300 import pc
     from paper_2308_07173_gb300 import workloads as W
 
+    from paper_2308_07173_gb300 import autotune
+
     pc.load()
     q, m = W.stress()
     md = torch.from_numpy(m).cuda()
-    t = pc.Target(md)
-    qd = torch.from_numpy(q).cuda()
     k = 32
+    tuned = autotune.lookup(autotune.default_cache(), k, len(m), len(q))
+    cfg = dict(autotune.DEFAULT, **(tuned or {}))
+    t = autotune.apply(md, cfg)
+    qd = torch.from_numpy(q).cuda()
     idx = torch.empty((len(q), k), dtype=torch.int32, device="cuda")
     d2 = torch.empty((len(q), k), dtype=torch.float32, device="cuda")
     cov = torch.empty((len(q), 6), dtype=torch.float32, device="cuda")
     flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
     s = torch.cuda.Stream()
-    t.stats(reset=True)
-    ms, _ = _timed(lambda: t.knn_cov(qd, k, EPS, idx, d2, cov, stream=s), flush, min(args.steps, 20), s)
-    st = t.stats(reset=True, stream=s)
-    assert t.sync_status(s) == pc.PC_OK
+    out = {}
+    for name, probe in (("per_query_start", 2), ("calibrated_start", 1)):
+        t.set_tune(cfg["tile"], cfg["warps"], cfg["rho_scale"], 0, probe, cfg["slots"])
+        clocks = Clocks(torch.cuda.current_device())
+        clocks.start()
+        ms, v = _timed(lambda: t.knn_cov(qd, k, EPS, idx, d2, cov, stream=s), flush, min(args.steps, 20), s)
+        clk = clocks.stop()
+        t.stats(reset=True, stream=s)
+        t.knn_cov(qd, k, EPS, idx, d2, cov, stream=s)
+        st = t.stats(reset=True, stream=s)
+        assert t.sync_status(s) == pc.PC_OK
+        out[name] = {"ms": ms, "value": len(q) / (ms / 1e3), "clocks": clk,
+                     "warp_search_frac": st["warp_search"] / max(1, st["queries"]),
+                     "exhaustive": st["exhaustive"], "candidates_per_query": st["candidates"] / max(1, st["queries"])}
     info = t.info()
-    alg = len(q) * (12 + 8 * k + 24)
-    peak, kind = peaks()
+    best = out["per_query_start"]
+    roof = algorithmic_roofline(md, info, [idx], len(q), k, best["ms"])
     _line("query points/sec, 1M queries vs 20M-point map (4 km + pit lane), kNN(k=32)+cov",
-          len(q) / (ms / 1e3), UNIT, ms, args,
+          best["value"], UNIT, best["ms"], args,
           {"workload": "c5_map20M_pit_noise1cm_queries1M_k32", "queries": len(q), "map_points": len(m),
-           "cell_size": info["cell_size"], "occupied_cells": info["ncells"]},
-          roofline={"bound": "hbm", "achieved": alg / (ms / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
-                    "frac": alg / (ms / 1e3) / 1e9 / peak, "peak_source": kind,
-                    "algorithmic_bytes_queries_only": alg},
-          search_paths={"warp_search_frac": st["warp_search"] / max(1, st["queries"]),
-                        "exhaustive": st["exhaustive"]})
+           "cell_size": info["cell_size"], "occupied_cells": info["ncells"],
+           "tuned": tuned or "defaults (no cached configuration)",
+           "start_radius": "per query, from the point count of the 27 cells around it (the target's default "
+                           "on this map: its calibration saw an uneven density)"},
+          roofline=roof, search_paths={"warp_search_frac": best["warp_search_frac"], "exhaustive": best["exhaustive"],
+                                       "candidates_per_query": best["candidates_per_query"]},
+          clocks=best["clocks"], calibrated_start=out["calibrated_start"], gpu_launches=1)
     return 0
 
 

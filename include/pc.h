@@ -92,6 +92,8 @@ typedef struct {
                           map whose calibration saw an even density, else 2); 1 the
                           calibrated radius for every query; 2 a per-query radius from
                           the point count of the 27 cells around it */
+    int slots;         /* survivor slots per query of the lane path (its k tile): 0 by
+                          k (32 for k <= 24, 64 for 25..32); 64 for every k <= 32 */
 } pc_tune;
 
 /* What the built target looks like (for reporting and tuning). */

@@ -7,17 +7,26 @@ cell size, launch shape or starting radius), so the tuner only times them:
   edge h of the voxel-hash grid (the target is rebuilt per value);
 * rho_scale -- the starting radius as a multiple of the calibrated k-th
   neighbour distance (the lane path's trial radii scale with it);
-* warps -- warps per block; tile (queries per warp item) stays 32, one per
-  lane of the lane path.
+* warps -- warps per block;
+* tile -- queries per warp work item (points per warp: 32 fills every lane
+  of the lane path, fewer leave lanes idle but shorten each item);
+* slots -- the lane path's survivor slots per query, its k tile: 32 (k <=
+  24) with eight trial radii, or 64 with four;
+* probe -- whether each query's trial radii start from the map's
+  calibrated radius (1) or from a per-query estimate from the point count
+  of the 27 cells around it (2).
 
-Each configuration is timed with CUDA events on the launching stream, L2
-flushed (a 256 MB write) before every timed call, and its outputs are
-compared bit for bit with the first configuration's.  The best result is
-cached per (GPU, k, target size, query count) in a JSON file.
+The search is a coordinate descent from the defaults: one parameter at a
+time over its values, keeping the best, for `rounds` rounds.  Each
+configuration is timed with CUDA events on the launching stream, L2 flushed
+(a 256 MB write) before every timed call, and its outputs are compared bit
+for bit with the first configuration's.  The best result is cached per
+(GPU, k, target size, query-count bucket) in a JSON file; the package's own
+cache (default_cache()) holds the configurations tuned for the benchmark
+workloads on GB300.
 """
 from __future__ import annotations
 
-import itertools
 import json
 import os
 from typing import Iterable, Optional
@@ -79,50 +88,130 @@ def _time_call(fn, flush, reps: int) -> float:
     return v[len(v) // 2]
 
 
-def tune(map_xyz, queries, k: int, eps: float, occupancies: Iterable[float] = (8, 12, 16),
-         rho_scales: Iterable[float] = (0.8, 0.9, 1.0), warps: Iterable[int] = (2, 4, 8),
-         reps: int = 15, cache: Optional[str] = None) -> dict:
-    """Time every combination on (map_xyz [M,3], queries [N,3]) CUDA float32
-    tensors; returns the best {occupancy, rho_scale, warps, tile, ms} plus
-    the whole grid, and stores the best in `cache` if given."""
+DEFAULT = {"occupancy": 12.0, "rho_scale": 0.9, "warps": 4, "tile": 32, "slots": 0, "probe": 0}
+SPACE = {"occupancy": (8.0, 12.0, 16.0), "rho_scale": (0.8, 0.9, 1.0), "warps": (2, 4, 8), "tile": (16, 32),
+         "slots": (0, 64), "probe": (1, 2)}
+
+
+def tune(map_xyz, queries, k: int, eps: float, space: Optional[dict] = None, rounds: int = 2, reps: int = 15,
+         cache: Optional[str] = None) -> dict:
+    """Coordinate descent over `space` (parameter -> values; SPACE by
+    default) on (map_xyz [M,3], queries [N,3]) CUDA float32 tensors; returns
+    the best configuration (with its time in ms and cell size) and every
+    configuration timed, and stores the best in `cache` if given."""
     import torch
 
+    space = dict(SPACE if space is None else space)
+    if k > 24:
+        space.pop("slots", None)  # 64 slots already
     n = queries.shape[0]
     dev = queries.device
     idx = torch.empty((n, k), dtype=torch.int32, device=dev)
     d2 = torch.empty((n, k), dtype=torch.float32, device=dev)
     cov = torch.empty((n, 6), dtype=torch.float32, device=dev)
     flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
-    ref = None
-    grid = []
-    for occ in occupancies:
-        t = pc.Target(map_xyz, occupancy=float(occ))
-        h = t.info()["cell_size"]
-        for rs, w in itertools.product(rho_scales, warps):
-            t.set_tune(32, int(w), float(rs))
-            ms = _time_call(lambda: t.knn_cov(queries, k, eps, idx, d2, cov), flush, reps)
-            out = (idx.clone(), d2.view(torch.int32).clone(), cov.view(torch.int32).clone())
-            if ref is None:
-                ref = out
-            elif not all(torch.equal(a, b) for a, b in zip(ref, out)):
-                raise RuntimeError(f"results changed with occupancy={occ} rho_scale={rs} warps={w}")
-            grid.append({"occupancy": float(occ), "cell_size": h, "rho_scale": float(rs), "warps": int(w),
-                         "tile": 32, "ms": ms})
+    targets = {}
+    timed = {}
+    ref = []
+
+    def target(occ):
+        if occ not in targets:
+            targets[occ] = pc.Target(map_xyz, occupancy=float(occ))
+        return targets[occ]
+
+    def measure(cfg):
+        key = tuple(sorted(cfg.items()))
+        if key in timed:
+            return timed[key]["ms"]
+        t = target(cfg["occupancy"])
+        t.set_tune(cfg["tile"], cfg["warps"], cfg["rho_scale"], 0, cfg["probe"], cfg["slots"])
+        ms = _time_call(lambda: t.knn_cov(queries, k, eps, idx, d2, cov), flush, reps)
+        out = (idx.clone(), d2.view(torch.int32).clone(), cov.view(torch.int32).clone())
+        if not ref:
+            ref.append(out)
+        elif not all(torch.equal(a, b) for a, b in zip(ref[0], out)):
+            raise RuntimeError(f"results changed with {cfg}")
+        timed[key] = dict(cfg, cell_size=t.info()["cell_size"], ms=ms)
+        return ms
+
+    best = dict(DEFAULT)
+    best_ms = measure(best)
+    for _ in range(rounds):
+        for name, values in space.items():
+            for v in values:
+                cfg = dict(best, **{name: v})
+                ms = measure(cfg)
+                if ms < best_ms:
+                    best, best_ms = cfg, ms
+    for t in targets.values():
         t.close()
-    best = dict(min(grid, key=lambda r: r["ms"]))
+    result = dict(timed[tuple(sorted(best.items()))])
     if cache:
         data = load_cache(cache)
-        data[_key(k, int(map_xyz.shape[0]), int(n))] = best
+        data[_key(k, int(map_xyz.shape[0]), int(n))] = result
         tmp = cache + ".tmp"
         os.makedirs(os.path.dirname(os.path.abspath(cache)), exist_ok=True)
         with open(tmp, "w") as f:
             json.dump(data, f, indent=1, sort_keys=True)
         os.replace(tmp, cache)
-    return {"best": best, "grid": grid}
+    return {"best": result, "grid": list(timed.values())}
 
 
 def apply(map_xyz, cfg: dict) -> "pc.Target":
     """Build a target with a tuned configuration."""
     t = pc.Target(map_xyz, occupancy=cfg["occupancy"])
-    t.set_tune(cfg.get("tile", 32), cfg["warps"], cfg["rho_scale"])
+    t.set_tune(cfg.get("tile", 32), cfg["warps"], cfg["rho_scale"], 0, cfg.get("probe", 0), cfg.get("slots", 0))
     return t
+
+
+def tune_workloads(names, cache: Optional[str] = None, rounds: int = 2, reps: int = 10) -> dict:
+    """Tunes the benchmark workloads on this GPU and stores their best
+    configurations in `cache` (the package's default cache by default):
+    c2 the 131k-point scan against the 2M-point map (k = 20), c3 the 64-scan
+    batch as one query set, c4 three served scans against the 5M-point map
+    (stored for any query count), c5 the 1M-query stress set against the
+    20M-point map (k = 32)."""
+    import numpy as np
+    import torch
+
+    from . import workloads as W
+
+    cache = cache or default_cache()
+    out = {}
+    for name in names:
+        if name == "c2":
+            q, m = W.scan_vs_map()
+            k, n_key = 20, len(q)
+        elif name == "c3":
+            _, m = W.scan_vs_map()
+            q = np.concatenate(W.scan_batch(64, seed=4))
+            k, n_key = 20, len(q)
+        elif name == "c4":
+            m = W.oval_1500().sample_map(5_000_000, seed=5)
+            q = np.concatenate([a.points for a in W.arrival_stream(duration=0.2, seed=5)[:3]])
+            k, n_key = 20, 0
+        elif name == "c5":
+            q, m = W.stress()
+            k, n_key = 32, len(q)
+        else:
+            raise ValueError(name)
+        md = torch.from_numpy(m).cuda()
+        qd = torch.from_numpy(np.ascontiguousarray(q)).cuda()
+        res = tune(md, qd, k, 1e-3, rounds=rounds, reps=reps)
+        best = res["best"]
+        data = load_cache(cache)
+        data[_key(k, int(md.shape[0]), n_key)] = best
+        with open(cache + ".tmp", "w") as f:
+            json.dump(data, f, indent=1, sort_keys=True)
+        os.replace(cache + ".tmp", cache)
+        out[name] = {"best": best, "default_ms": res["grid"][0]["ms"], "configs": len(res["grid"])}
+        print(name, json.dumps(out[name]), flush=True)
+        del md, qd
+        torch.cuda.empty_cache()
+    return out
+
+
+if __name__ == "__main__":
+    import sys
+
+    tune_workloads(sys.argv[1].split(",") if len(sys.argv) > 1 else ["c2", "c3", "c4", "c5"])

@@ -60,6 +60,13 @@ cudaError_t ensure_attrs() {
 }
 
 int clamp_tile(int t) { return t <= 0 ? 32 : (t > 32 ? 32 : t); }
+
+// The search mode for k on this target: its tune may ask for 64 survivor
+// slots (mode 1) for every k <= 32.
+int target_mode(const pc_target_s* t, int k) {
+    const int m = search_mode(k);
+    return (m == 0 && t->tune.slots == 64) ? 1 : m;
+}
 int clamp_warps(int w) { return w <= 0 ? 4 : (w > 8 ? 8 : w); }
 
 // Calls f(kernel) with the search kernel for (mode, with_cov, windowed).
@@ -84,7 +91,7 @@ cudaError_t pc_launch_knn(const pc_target_s* t, const float* q, int64_t N, int k
     TileArgs a{k, eps, t->tune.rho_scale > 0 ? t->tune.rho_scale : 0.9f, t->tune.order == 0 ? 1 : 0, t->ck,
                pc_probe_c(t)};
     const bool with_cov = cov != nullptr;
-    const int mode = search_mode(k);
+    const int mode = target_mode(t, k);
     const size_t smem = (size_t)warps * warp_smem_bytes(mode);
     const int64_t tiles = (N + tile - 1) / tile;
     const int64_t blocks = (tiles + warps - 1) / warps;
@@ -108,7 +115,7 @@ cudaError_t pc_launch_knn_union(const pc_target_s* t, const float* q, int64_t N,
     TileArgs a{k, eps, t->tune.rho_scale > 0 ? t->tune.rho_scale : 0.9f, t->tune.order == 0 ? 1 : 0, t->ck,
                pc_probe_c(t)};
     const bool with_cov = cov != nullptr;
-    const int mode = search_mode(k);
+    const int mode = target_mode(t, k);
     const size_t smem = (size_t)warps * warp_smem_bytes(mode);
     const int64_t tiles = (N + tile - 1) / tile;
     const int64_t blocks = (tiles + warps - 1) / warps;
@@ -142,7 +149,7 @@ cudaError_t pc_launch_knn_batch(const pc_target_s* t, const Grid& gv, const CovK
                pc_probe_c(t)};
     const int64_t blocks = (total_tiles + warps - 1) / warps;
     if (blocks > 0x7fffffff) return cudaErrorInvalidValue;
-    const int mode = search_mode(k);
+    const int mode = target_mode(t, k);
     const size_t smem = (size_t)warps * warp_smem_bytes(mode);
     Grid g = gv;
     void* args[] = {&g, (void*)&scans_dev, &nscans, &total_tiles, &tile, &a, &rho0};

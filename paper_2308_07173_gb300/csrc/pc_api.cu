@@ -70,6 +70,7 @@ void default_tune(pc_tune* tu) {
     tu->rho_scale = 0.9f;
     tu->order = 0;
     tu->probe = 0;
+    tu->slots = 0;
 }
 
 pc_status read_and_clear_status(pc_target_s* t, cudaStream_t s) {
@@ -283,7 +284,7 @@ pc_status pc_set_tune(pc_target t, const pc_tune* tune) {
         return PC_OK;
     }
     if (tune->tile > 32 || tune->warps > 8 || !(std::isfinite(tune->rho_scale)) || tune->order < 0 ||
-        tune->order > 1 || tune->probe < 0 || tune->probe > 2)
+        tune->order > 1 || tune->probe < 0 || tune->probe > 2 || (tune->slots != 0 && tune->slots != 64))
         return PC_ERR_INVALID_ARG;
     t->tune = *tune;
     if (t->tune.tile <= 0) t->tune.tile = 32;

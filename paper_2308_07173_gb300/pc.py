@@ -92,7 +92,7 @@ class pc_window(ctypes.Structure):
 
 class pc_tune(ctypes.Structure):
     _fields_ = [("tile", ctypes.c_int), ("warps", ctypes.c_int), ("rho_scale", ctypes.c_float),
-                ("order", ctypes.c_int), ("probe", ctypes.c_int)]
+                ("order", ctypes.c_int), ("probe", ctypes.c_int), ("slots", ctypes.c_int)]
 
 
 class pc_target_info(ctypes.Structure):
@@ -270,6 +270,12 @@ def pc_batch_run_scratch(t, scans: Sequence[pc_scan], k: int, eps: float, scratc
     return load().pc_batch_run_scratch(t, arr, len(scans), k, eps, scratch_dev, scratch_bytes, stream)
 
 
+def pc_batch_run_scratch_array(t, arr, n: int, k: int, eps: float, scratch_dev: int, scratch_bytes: int,
+                               stream) -> int:
+    """pc_batch_run_scratch on a ready ctypes array of n pc_scan."""
+    return load().pc_batch_run_scratch(t, arr, n, k, eps, scratch_dev, scratch_bytes, stream)
+
+
 def pc_set_window(t, lo=None, hi=None) -> int:
     if lo is None:
         return load().pc_set_window(t, None)
@@ -381,8 +387,9 @@ class Target:
             "delta_m": i.delta_m,
         }
 
-    def set_tune(self, tile: int = 0, warps: int = 0, rho_scale: float = 0.0, order: int = 0, probe: int = 0):
-        pc_set_tune(self.handle, pc_tune(tile, warps, rho_scale, order, probe))
+    def set_tune(self, tile: int = 0, warps: int = 0, rho_scale: float = 0.0, order: int = 0, probe: int = 0,
+                 slots: int = 0):
+        pc_set_tune(self.handle, pc_tune(tile, warps, rho_scale, order, probe, slots))
 
     def knn(self, q, k: int, idx=None, d2=None, stream=None):
         torch = _torch()

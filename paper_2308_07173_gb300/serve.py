@@ -11,9 +11,12 @@ GPU).  The map's grid stays resident on the device.  The loop:
   HBM budget left after the step slots' fixed scratch, and a step slot is
   free;
 * launches each admitted group as ONE batched kernel (pc_batch_run_scratch)
-  on the slot's own stream: host-to-device copies, the batched kernel and
-  device-to-host copies are queued on that stream, so a new step's copies
-  and kernel overlap the steps already on the GPU;
+  on the slot's own stream: host-to-device copies into the slot's device
+  buffers, the batched kernel and device-to-host copies into the slot's
+  pinned buffers are queued on that stream, so a new step's copies and
+  kernel overlap the steps already on the GPU (a slot's buffers grow to its
+  largest step and are reused, so a step allocates nothing in the common
+  case);
 * retires steps whose completion event has fired, frees their bytes and
   slot, and stamps each request's completion time.
 
@@ -145,39 +148,71 @@ class Server:
         self.request_budget = max(0, self.budget - self.fixed_bytes)
         self.steps_launched = 0
         self.keep = keep_results
+        self.slot_buf = [None] * slots
 
     def request_bytes(self, n: int) -> int:
         """Device bytes one request holds while in flight: its scan, idx, d2
         and cov tensors, each rounded up to the allocator's block size."""
         return (_blocks(12 * n) + _blocks(4 * self.k * n) + _blocks(4 * self.k * n) + _blocks(24 * n))
 
+    def _slot_buffers(self, slot: int, npts: int):
+        """The slot's device and pinned host buffers, grown to hold npts
+        points (q, idx, d2, cov each), so a step allocates nothing in the
+        common case."""
+        import torch
+
+        have = self.slot_buf[slot]
+        if have is not None and have[0] >= npts:
+            return have
+        cap = max(npts, 1 << 17)
+        k = self.k
+        dev = (torch.empty((cap, 3), dtype=torch.float32, device=self.dev),
+               torch.empty((cap, k), dtype=torch.int32, device=self.dev),
+               torch.empty((cap, k), dtype=torch.float32, device=self.dev),
+               torch.empty((cap, 6), dtype=torch.float32, device=self.dev))
+        host = _pinned_outputs(cap, k)
+        self.slot_buf[slot] = (cap, dev, host)
+        return self.slot_buf[slot]
+
     def _launch(self, slot: int, reqs: List[Request]) -> _Step:
         import torch
 
         s = self.streams[slot]
-        k = self.k
-        descs = []
+        npts = sum(r.n for r in reqs)
+        _, (dq, di, dd, dc), (hi, hd, hc) = self._slot_buffers(slot, npts)
+        descs = (pc.pc_scan * len(reqs))()
         with torch.cuda.stream(s):
-            for r in reqs:
-                q = r.q_host.to(self.dev, non_blocking=True)
-                idx = torch.empty((r.n, k), dtype=torch.int32, device=self.dev)
-                d2 = torch.empty((r.n, k), dtype=torch.float32, device=self.dev)
-                cov = torch.empty((r.n, 6), dtype=torch.float32, device=self.dev)
-                r.dev = (q, idx, d2, cov)
-                descs.append(pc.pc_scan(q.data_ptr(), r.n, idx.data_ptr(), d2.data_ptr(), cov.data_ptr()))
-            rc = pc.pc_batch_run_scratch(self.t.handle, descs, k, self.eps, self.scratch[slot].data_ptr(),
-                                         self.scratch_bytes, int(s.cuda_stream))
+            off = 0
+            for j, r in enumerate(reqs):
+                n = r.n
+                dq[off:off + n].copy_(r.q_host, non_blocking=True)
+                descs[j] = pc.pc_scan(dq[off].data_ptr() if n else 0, n, di[off].data_ptr() if n else 0,
+                                      dd[off].data_ptr() if n else 0, dc[off].data_ptr() if n else 0)
+                r.dev = (off, n)
+                off += n
+            rc = pc.pc_batch_run_scratch_array(self.t.handle, descs, len(reqs), self.k, self.eps,
+                                               self.scratch[slot].data_ptr(), self.scratch_bytes,
+                                               int(s.cuda_stream))
             if rc != pc.PC_OK:
                 raise pc.PcError(rc, "pc_batch_run_scratch")
-            for r in reqs:
-                if not r.out_host:
-                    r.out_host = _pinned_outputs(r.n, k)
-                for host, devt in zip(r.out_host, r.dev[1:]):
-                    host.copy_(devt, non_blocking=True)
+            if npts:
+                hi[:npts].copy_(di[:npts], non_blocking=True)
+                hd[:npts].copy_(dd[:npts], non_blocking=True)
+                hc[:npts].copy_(dc[:npts], non_blocking=True)
             done = torch.cuda.Event()
             done.record(s)
         self.steps_launched += 1
         return _Step(slot, reqs, done, sum(self.request_bytes(r.n) for r in reqs))
+
+    def _retire(self, st: _Step):
+        """Results of a finished step: views of the slot's pinned buffers
+        (copied out when the caller keeps them, since the slot is reused)."""
+        _, _, (hi, hd, hc) = self.slot_buf[st.slot]
+        for r in st.reqs:
+            off, n = r.dev
+            if self.keep:
+                r.out_host = (hi[off:off + n].clone(), hd[off:off + n].clone(), hc[off:off + n].clone())
+            r.dev = ()
 
     def serve(self, reqs: Sequence[Request], speed: float = 1.0) -> dict:
         """Replay the arrivals (times divided by `speed`) and serve them."""
@@ -202,11 +237,9 @@ class Server:
             for st in list(inflight):
                 if st.done.query():
                     tdone = time.perf_counter() - t0
+                    self._retire(st)
                     for r in st.reqs:
                         r.t_done = tdone
-                        r.dev = ()
-                        if not self.keep:
-                            r.out_host = ()
                     used -= st.nbytes
                     free_slots.append(st.slot)
                     inflight.remove(st)
