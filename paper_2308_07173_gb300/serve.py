@@ -6,19 +6,20 @@ GPU).  The map's grid stays resident on the device.  The loop:
 
 * moves arrived requests to a pending queue (arrival times are replayed in
   real time, optionally sped up);
-* admits pending requests while their device bytes (scan + idx + d2 + cov,
-  each rounded up to the caching allocator's 512-byte blocks) fit in the
-  HBM budget left after the step slots' fixed scratch, and a step slot is
-  free;
-* launches each admitted group as ONE batched kernel (pc_batch_run_scratch)
-  on the slot's own stream: host-to-device copies into the slot's device
-  buffers, the batched kernel and device-to-host copies into the slot's
-  pinned buffers are queued on that stream, so a new step's copies and
-  kernel overlap the steps already on the GPU (a slot's buffers grow to its
-  largest step and are reused, so a step allocates nothing in the common
-  case);
-* retires steps whose completion event has fired, frees their bytes and
-  slot, and stamps each request's completion time.
+* sizes each of its step slots once, from the HBM budget: a slot holds the
+  scan, idx, d2 and cov of up to `capacity` points on the device and the
+  same outputs in pinned host memory, allocated at start-up and reused by
+  every step (so serving allocates nothing);
+* admits pending requests into a step (FIFO) while the step has fewer than
+  `max_step` scans and its points fit the slot's capacity, when a slot is
+  free; a single scan larger than the capacity runs alone on buffers grown
+  for it;
+* launches each step as ONE batched kernel (pc_batch_run_scratch) on the
+  slot's own stream: host-to-device copies, the batched kernel and
+  device-to-host copies are queued on that stream, so a new step's copies
+  and kernel overlap the steps already on the GPU;
+* retires steps whose completion event has fired, frees their slot, and
+  stamps each request's completion time.
 
 Latency is completion minus arrival.  ``serve_per_scan`` is the baseline:
 one synchronous host-buffer call (pc_knn_cov_host) per scan in arrival
@@ -92,21 +93,22 @@ def _pinned_outputs(n: int, k: int):
             torch.empty((n, 6), dtype=torch.float32, pin_memory=True))
 
 
-def admit(pending: deque, used: int, budget: int, max_step: int, busy: bool, nbytes) -> tuple:
+def admit(pending: deque, max_step: int, capacity: int) -> list:
     """One step's admission: take requests from the head of `pending` (FIFO)
-    while the step has fewer than `max_step` and their device bytes
-    (`nbytes(n)`) fit in `budget` beside the `used` bytes in flight.  A head
-    request larger than the whole budget is admitted alone when nothing is
-    in flight (`busy` false), so the queue never stalls; otherwise a request
-    that does not fit waits for retirements.  Returns (batch, used)."""
+    while the step has fewer than `max_step` and their points fit in
+    `capacity`.  A head request larger than the whole capacity is admitted
+    alone, so the queue never stalls.  Returns the step's requests."""
     batch = []
+    pts = 0
     while pending and len(batch) < max_step:
-        b = nbytes(pending[0].n)
-        if used + b > budget and (batch or busy):
+        n = pending[0].n
+        if batch and pts + n > capacity:
             break
         batch.append(pending.popleft())
-        used += b
-    return batch, used
+        pts += n
+        if pts > capacity:  # a lone oversized head
+            break
+    return batch
 
 
 ALLOC_BLOCK = 512  # torch's caching allocator rounds every block up to this
@@ -121,12 +123,18 @@ class _Step:
     slot: int
     reqs: List[Request]
     done: object
-    nbytes: int
 
 
 class Server:
+    """Continuous batching over a resident target.  hbm_budget (bytes; half
+    the free device memory by default) sizes the slots: each slot's scan
+    table and per-point buffers (12 + 8k + 24 bytes a point) share it, so a
+    step holds up to capacity = (budget / slots - table) / point bytes
+    points, capped by max_step_points."""
+
     def __init__(self, target: "pc.Target", k: int, eps: float, hbm_budget: Optional[int] = None,
-                 max_step_scans: int = 32, slots: int = 3, keep_results: bool = False):
+                 max_step_scans: int = 32, slots: int = 3, keep_results: bool = False,
+                 max_step_points: int = 1 << 20):
         import torch
 
         self.t = target
@@ -142,36 +150,33 @@ class Server:
         self.scratch_bytes = pc.pc_batch_scratch_bytes(self.max_step)
         self.scratch = [torch.empty(self.scratch_bytes, dtype=torch.uint8, device=self.dev)
                         for _ in range(slots)]
-        # the slots' scan tables are held for the server's lifetime: the
-        # requests share what is left of the budget
-        self.fixed_bytes = slots * _blocks(self.scratch_bytes)
-        self.request_budget = max(0, self.budget - self.fixed_bytes)
+        self.point_bytes = 12 + 8 * self.k + 24
+        per_slot = self.budget // slots - _blocks(self.scratch_bytes) - 4 * ALLOC_BLOCK
+        self.capacity = int(max(1, min(int(max_step_points), per_slot // self.point_bytes)))
+        self.slot_buf = [self._alloc(self.capacity) for _ in range(slots)]
         self.steps_launched = 0
         self.keep = keep_results
-        self.slot_buf = [None] * slots
 
-    def request_bytes(self, n: int) -> int:
-        """Device bytes one request holds while in flight: its scan, idx, d2
-        and cov tensors, each rounded up to the allocator's block size."""
-        return (_blocks(12 * n) + _blocks(4 * self.k * n) + _blocks(4 * self.k * n) + _blocks(24 * n))
+    def device_bytes(self) -> int:
+        """Device memory the server holds: the slots' tables and buffers."""
+        return sum(_blocks(self.scratch_bytes) + sum(_blocks(x.numel() * x.element_size()) for x in b[1])
+                   for b in self.slot_buf)
 
-    def _slot_buffers(self, slot: int, npts: int):
-        """The slot's device and pinned host buffers, grown to hold npts
-        points (q, idx, d2, cov each), so a step allocates nothing in the
-        common case."""
+    def _alloc(self, cap: int):
         import torch
 
-        have = self.slot_buf[slot]
-        if have is not None and have[0] >= npts:
-            return have
-        cap = max(npts, 1 << 17)
         k = self.k
         dev = (torch.empty((cap, 3), dtype=torch.float32, device=self.dev),
                torch.empty((cap, k), dtype=torch.int32, device=self.dev),
                torch.empty((cap, k), dtype=torch.float32, device=self.dev),
                torch.empty((cap, 6), dtype=torch.float32, device=self.dev))
-        host = _pinned_outputs(cap, k)
-        self.slot_buf[slot] = (cap, dev, host)
+        return (cap, dev, _pinned_outputs(cap, k))
+
+    def _slot_buffers(self, slot: int, npts: int):
+        """The slot's buffers; a lone scan above the capacity gets buffers
+        grown for it (kept for the slot's later steps)."""
+        if self.slot_buf[slot][0] < npts:
+            self.slot_buf[slot] = self._alloc(npts)
         return self.slot_buf[slot]
 
     def _launch(self, slot: int, reqs: List[Request]) -> _Step:
@@ -202,7 +207,7 @@ class Server:
             done = torch.cuda.Event()
             done.record(s)
         self.steps_launched += 1
-        return _Step(slot, reqs, done, sum(self.request_bytes(r.n) for r in reqs))
+        return _Step(slot, reqs, done)
 
     def _retire(self, st: _Step):
         """Results of a finished step: views of the slot's pinned buffers
@@ -225,7 +230,6 @@ class Server:
         pending: deque = deque()
         inflight: List[_Step] = []
         free_slots = list(range(len(self.streams)))
-        used = 0
         nxt = 0
         done = 0
         t0 = time.perf_counter()
@@ -240,21 +244,20 @@ class Server:
                     self._retire(st)
                     for r in st.reqs:
                         r.t_done = tdone
-                    used -= st.nbytes
                     free_slots.append(st.slot)
                     inflight.remove(st)
                     done += len(st.reqs)
             if pending and free_slots:
-                batch, used = admit(pending, used, self.request_budget, self.max_step, bool(inflight),
-                                    self.request_bytes)
-                peak = max(peak, used)
+                batch = admit(pending, self.max_step, self.capacity)
+                peak = max(peak, sum(r.n for r in batch))
                 for r in batch:
                     r.t_admit = now
-                if not batch and pending[0].rid not in waited:
-                    waited.add(pending[0].rid)  # the head request waits for bytes to be freed
-                if batch:
-                    inflight.append(self._launch(free_slots.pop(0), batch))
-                    continue
+                inflight.append(self._launch(free_slots.pop(0), batch))
+                if pending and pending[0].rid not in waited:
+                    waited.add(pending[0].rid)  # did not fit this step: waits for a slot
+                continue
+            if pending and not free_slots and pending[0].rid not in waited:
+                waited.add(pending[0].rid)  # every slot busy
             if not pending and not inflight and nxt < len(reqs):
                 wait = reqs[nxt].t_sched - (time.perf_counter() - t0)
                 if wait > 2e-4:
@@ -263,9 +266,10 @@ class Server:
         out = latency_report(reqs, wall)
         out["steps"] = self.steps_launched
         out["mean_scans_per_step"] = len(reqs) / max(1, self.steps_launched)
-        out["admission_waits"] = len(waited)  # requests that waited for budget
-        out["peak_request_bytes"] = peak
-        out["request_budget"] = self.request_budget
+        out["admission_waits"] = len(waited)  # requests that waited for a slot or a step's room
+        out["peak_step_points"] = peak
+        out["capacity_points"] = self.capacity
+        out["device_bytes"] = self.device_bytes()
         return out
 
 

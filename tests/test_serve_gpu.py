@@ -39,7 +39,7 @@ def test_served_results_equal_alone(small_world, gpu_lib, speed):
     reqs = serve.requests_from_arrivals(arr)
     assert len(reqs) > 10
     serve.prepare(reqs)
-    srv = serve.Server(t, k, eps, hbm_budget=64 << 20, max_step_scans=4, slots=2, keep_results=True)
+    srv = serve.Server(t, k, eps, hbm_budget=256 << 20, max_step_scans=4, slots=2, keep_results=True)
     rep = srv.serve(reqs, speed=speed)
     assert rep["scans"] == len(reqs) and rep["p99_ms"] >= rep["p50_ms"] > 0
     if speed > 1:
@@ -86,29 +86,33 @@ def test_tiny_budget_serves_one_scan_at_a_time(small_world, gpu_lib):
     reqs = serve.requests_from_arrivals(arr[:10])
     serve.prepare(reqs)
     srv = serve.Server(t, k, eps, hbm_budget=1, max_step_scans=8, slots=2, keep_results=True)
+    assert srv.capacity == 1
     rep = srv.serve(reqs, speed=1e6)
-    assert rep["scans"] == 10 and rep["steps"] == 10  # the budget admits one request per step
+    assert rep["scans"] == 10 and rep["steps"] == 10  # every scan exceeds the capacity: one per step
     for r in reqs:
         assert _same(r.out_host, _alone(t, r.points, k, eps))
 
 
 def test_budget_that_forces_waits(small_world, gpu_lib):
-    """A budget with room for about two requests beside the slots' scratch:
-    requests that arrive together wait for earlier ones to retire, the bytes
-    in flight never exceed the budget, and every result is still the one the
-    scan gets alone."""
+    """A budget that gives each of two slots room for about two scans:
+    requests that arrive together wait for a slot or for room in a step,
+    no step exceeds the capacity the budget allows, the server holds no more
+    device memory than the budget, and every result is still the one the scan
+    gets alone."""
     t, arr = small_world
     k, eps = 20, 1e-3
     reqs = serve.requests_from_arrivals(arr)
     serve.prepare(reqs)
-    probe = serve.Server(t, k, eps, hbm_budget=1 << 30, max_step_scans=4, slots=2)
-    biggest = max(probe.request_bytes(r.n) for r in reqs)
-    budget = probe.fixed_bytes + int(2.2 * biggest)
+    biggest = max(r.n for r in reqs)
+    point_bytes = 12 + 8 * k + 24
+    budget = 2 * (int(2.2 * biggest) * point_bytes + (1 << 16))
     srv = serve.Server(t, k, eps, hbm_budget=budget, max_step_scans=4, slots=2, keep_results=True)
+    assert biggest <= srv.capacity < 3 * biggest
+    assert srv.device_bytes() <= budget
     rep = srv.serve(reqs, speed=1e6)
     assert rep["scans"] == len(reqs)
     assert rep["admission_waits"] > 0
-    assert rep["peak_request_bytes"] <= srv.request_budget
+    assert rep["peak_step_points"] <= srv.capacity
     for r in reqs:
         assert _same(r.out_host, _alone(t, r.points, k, eps))
     assert t.sync_status() == gpu_lib.PC_OK
