@@ -135,8 +135,9 @@ class Clocks:
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu_index: int):
+    def __init__(self, gpu_index: int, interval_ms: int = 50):
         self.idx = gpu_index
+        self.interval = int(interval_ms)
         self.proc = None
         self.path = None
 
@@ -146,7 +147,7 @@ class Clocks:
             os.close(fd)
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "50", "-f", self.path], stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+                 "-lms", str(self.interval), "-f", self.path], stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
             time.sleep(0.3)
         except Exception:
             self.proc = None
@@ -653,7 +654,9 @@ def measure_c4(duration: float, speeds, map_points: int = 5_000_000, warm_scans:
            "offered_points_per_s_at_1x": npts / duration, "hbm_budget_bytes": 2 << 30,
            "max_step_scans": 16, "slots": 3, "tuned": tuned or "defaults (no cached configuration)"}
     for name, speed in speeds:
-        clocks = Clocks(torch.cuda.current_device())
+        # host-timed latencies: sample clocks sparsely, so the sampler's own
+        # driver queries do not add to them
+        clocks = Clocks(torch.cuda.current_device(), interval_ms=200)
         clocks.start()
         sv = srv.serve(reqs, speed=speed)
         ps = serve.serve_per_scan(t, K_NN, EPS, reqs, speed=speed)

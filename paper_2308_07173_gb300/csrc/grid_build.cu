@@ -364,6 +364,23 @@ __global__ void k_occ_set(const u64* __restrict__ cell_keys, int64_t U, int bx, 
     atomicOr(&occ[L >> 5], 1u << (uint32_t)(L & 31));
 }
 
+// Dense starts from the row index: for every linear cell index L of the
+// grid (and L = ngrid), the rank u of the first occupied cell at or after
+// L, read through the bitmap and the word ranks, gives dstart[L] =
+// cell_start[u].
+__global__ void k_dstart(const uint32_t* __restrict__ occ, const uint32_t* __restrict__ rank,
+                         const uint32_t* __restrict__ cell_start, int64_t ngrid, uint32_t ncells,
+                         uint32_t* __restrict__ dstart) {
+    const int64_t L = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (L > ngrid) return;
+    uint32_t u = ncells;
+    if (L < ngrid) {
+        const int64_t w = L >> 5;
+        u = rank[w] + (uint32_t)__popc(occ[w] & ((1u << (uint32_t)(L & 31)) - 1u));
+    }
+    dstart[L] = cell_start[u];
+}
+
 __global__ void k_popc(const uint32_t* __restrict__ occ, int64_t nw, uint32_t* __restrict__ out) {
     const int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (w < nw) out[w] = (uint32_t)__popc(occ[w]);
@@ -497,7 +514,7 @@ cudaError_t count_cells(const float* xyz, int64_t M, const float o[3], float h, 
 
 void pc_free_grid(pc_target_s* t) {
     void* ps[] = {t->table, t->pts, t->xyz, t->cell_keys, t->cell_start, t->status, t->stage,
-                  t->occ, t->rank};
+                  t->occ, t->rank, t->dstart};
     for (void* p : ps)
         if (p) cudaFree(p);
     t->table = nullptr;
@@ -507,6 +524,7 @@ void pc_free_grid(pc_target_s* t) {
     t->status = nullptr;
     t->occ = nullptr;
     t->rank = nullptr;
+    t->dstart = nullptr;
     t->stage = nullptr;
     t->stage_bytes = 0;
 }
@@ -632,7 +650,7 @@ pc_status pc_build_grid(const float* xyz, int64_t M, const pc_build_opts& opts, 
 
     // 6b. row index: occupancy bitmap over the grid + rank per 32-cell word
     const int64_t ngrid = (int64_t)dims[0] * dims[1] * dims[2];
-    int64_t nwords = 0;
+    int64_t nwords = 0, dense_words = 0;
     if (ngrid <= ((int64_t)1 << 36)) {
         nwords = (ngrid + 31) / 32;
         PC_TRY(cudaMalloc(&t->occ, sizeof(uint32_t) * (size_t)nwords));
@@ -645,6 +663,14 @@ pc_status pc_build_grid(const float* xyz, int64_t M, const pc_build_opts& opts, 
         k_popc<<<grid_for(nwords, 256), 256, 0, s>>>(t->occ, nwords, pop);
         PC_TRY(cudaGetLastError());
         PC_TRY(scan_exclusive(pop, t->rank, nwords, tot2, sc, s));
+        // dense starts when they cost at most eight times the points' copy
+        if (ngrid < ((int64_t)1 << 31) && (ngrid + 1) * 4 <= 8 * 16 * M) {
+            PC_TRY(cudaMalloc(&t->dstart, sizeof(uint32_t) * (size_t)(ngrid + 1)));
+            k_dstart<<<grid_for(ngrid + 1, 256), 256, 0, s>>>(t->occ, t->rank, t->cell_start, ngrid, U,
+                                                              t->dstart);
+            PC_TRY(cudaGetLastError());
+            dense_words = ngrid + 1;
+        }
     }
 
     // 7. float4 copies
@@ -678,11 +704,12 @@ pc_status pc_build_grid(const float* xyz, int64_t M, const pc_build_opts& opts, 
     g.cell_start = t->cell_start;
     g.occ = t->occ;
     g.rank = t->rank;
+    g.dstart = t->dstart;
     g.status = t->status;
     g.stats = reinterpret_cast<unsigned long long*>(reinterpret_cast<char*>(t->status) + 32);
     pc_clear_window(g);
     t->device_bytes = (int64_t)(sizeof(uint4) * t->table_cap + 2 * sizeof(float4) * M +
                                 sizeof(u64) * U + sizeof(uint32_t) * (U + 1) + 64 +
-                                2 * sizeof(uint32_t) * nwords);
+                                2 * sizeof(uint32_t) * nwords + sizeof(uint32_t) * dense_words);
     return PC_OK;
 }

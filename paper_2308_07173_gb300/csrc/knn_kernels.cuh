@@ -746,10 +746,7 @@ __device__ __forceinline__ float probe_radius(const Grid& g, float qx, float qy,
     uint32_t n = 0;
     if (g.occ && x0 <= x1)
         for (int z = z0; z <= z1; ++z)
-            for (int y = y0; y <= y1; ++y) {
-                const uint2 u = row_cell_ranks(g, y, z, x0, x1);
-                if (u.y > u.x) n += __ldg(&g.cell_start[u.y]) - __ldg(&g.cell_start[u.x]);
-            }
+            for (int y = y0; y <= y1; ++y) n += row_range(g, y, z, x0, x1).y;
     const float cap = 3.0f * g.h;
     return n > 0 ? fminf(c * g.h * sqrtf((float)k / (float)n), cap) : cap;
 }

@@ -741,6 +741,7 @@ pc_status pc_target_compact(pc_target t, pc_stream s) {
     t->cell_start = n->cell_start;
     t->occ = n->occ;
     t->rank = n->rank;
+    t->dstart = n->dstart;
     t->status = n->status;
     delete n;  // its buffers now belong to t
     free_delta(t);

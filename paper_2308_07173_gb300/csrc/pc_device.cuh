@@ -46,6 +46,11 @@ struct Grid {
     // run of cells along x maps to one contiguous range of pts.
     const uint32_t* occ;
     const uint32_t* rank;
+    // Dense starts (null when the grid is too large for them): dstart[L] is
+    // the position in pts of the first point of the occupied cells with
+    // linear index >= L, for L in [0, dimx dimy dimz]; a row's run of cells
+    // is then one pair of loads, without the bitmap.
+    const uint32_t* dstart;
     int* status;
     unsigned long long* stats;  // [0] queries, [1] warp-search fallbacks, [2] exhaustive scans,
                                 // [3] lane-path candidate points
@@ -119,6 +124,11 @@ __device__ __forceinline__ uint2 row_cell_ranks(const Grid& g, int cy, int cz, i
 // Points of the occupied cells x0..x1 (x0 <= x1) of row (cy, cz) as one
 // range (start, count) of pts, through the row index.
 __device__ __forceinline__ uint2 row_range(const Grid& g, int cy, int cz, int x0, int x1) {
+    if (g.dstart) {
+        const int64_t base = (int64_t)g.dimx * ((int64_t)cy + (int64_t)g.dimy * cz);
+        const uint32_t s = __ldg(&g.dstart[base + x0]);
+        return make_uint2(s, __ldg(&g.dstart[base + x1 + 1]) - s);
+    }
     const uint2 u = row_cell_ranks(g, cy, cz, x0, x1);
     if (u.y == u.x) return make_uint2(0u, 0u);
     const uint32_t s = __ldg(&g.cell_start[u.x]);

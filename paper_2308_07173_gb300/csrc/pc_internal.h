@@ -50,6 +50,7 @@ struct pc_target_s {
     uint32_t* cell_start;
     uint32_t* occ;
     uint32_t* rank;
+    uint32_t* dstart;
     int* status;  // 64 bytes: status word, then 4 u64 statistics counters at +32
     // staging for pc_knn_cov_host, grown on demand
     void* stage;

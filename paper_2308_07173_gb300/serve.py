@@ -28,6 +28,7 @@ alone and in the mix.
 """
 from __future__ import annotations
 
+import gc
 import time
 from collections import deque
 from dataclasses import dataclass, field
@@ -62,6 +63,7 @@ class Request:
 def latency_report(reqs: Sequence[Request], wall: float) -> dict:
     lat = np.array([r.latency for r in reqs]) * 1e3
     pts = sum(r.n for r in reqs)
+    worst = int(np.argmax(lat))
     return {
         "scans": len(reqs),
         "points": int(pts),
@@ -69,6 +71,8 @@ def latency_report(reqs: Sequence[Request], wall: float) -> dict:
         "p99_ms": float(np.percentile(lat, 99)),
         "mean_ms": float(lat.mean()),
         "max_ms": float(lat.max()),
+        "max_at_s": float(reqs[worst].t_sched),  # when (in the replay) the slowest scan arrived
+        "over_10ms": int((lat > 10.0).sum()),
         "wall_s": wall,
         "throughput_pts_s": pts / wall if wall > 0 else float("nan"),
     }
@@ -220,7 +224,18 @@ class Server:
             r.dev = ()
 
     def serve(self, reqs: Sequence[Request], speed: float = 1.0) -> dict:
-        """Replay the arrivals (times divided by `speed`) and serve them."""
+        """Replay the arrivals (times divided by `speed`) and serve them
+        (the garbage collector is paused meanwhile, as in a latency-bound
+        service loop)."""
+        paused = gc.isenabled()
+        gc.disable()
+        try:
+            return self._serve(reqs, speed)
+        finally:
+            if paused:
+                gc.enable()
+
+    def _serve(self, reqs: Sequence[Request], speed: float) -> dict:
         reqs = sorted(reqs, key=lambda r: r.t_arrival)
         for r in reqs:
             r.t_sched = r.t_arrival / speed
@@ -277,12 +292,25 @@ def serve_per_scan(target: "pc.Target", k: int, eps: float, reqs: Sequence[Reque
                    stream=None, keep_results: bool = False) -> dict:
     """Baseline: each scan in arrival order through one synchronous
     host-buffer call (copies in, kernel, copies out)."""
+    paused = gc.isenabled()
+    gc.disable()
+    try:
+        return _per_scan(target, k, eps, reqs, speed, stream, keep_results)
+    finally:
+        if paused:
+            gc.enable()
+
+
+def _per_scan(target, k, eps, reqs, speed, stream, keep_results) -> dict:
     import torch
 
     reqs = sorted(reqs, key=lambda r: r.t_arrival)
     for r in reqs:
         r.t_sched = r.t_arrival / speed
     stream = stream or torch.cuda.Stream(target.device)
+    # one set of pinned outputs for the largest scan, allocated before the
+    # replay (a service would hold them), unless every result is kept
+    shared = None if keep_results else _pinned_outputs(max(r.n for r in reqs), k)
     t0 = time.perf_counter()
     for r in reqs:
         wait = r.t_sched - (time.perf_counter() - t0)
@@ -291,7 +319,10 @@ def serve_per_scan(target: "pc.Target", k: int, eps: float, reqs: Sequence[Reque
         while time.perf_counter() - t0 < r.t_sched:
             pass
         r.t_admit = time.perf_counter() - t0
-        out = r.out_host if r.out_host else _pinned_outputs(r.n, k)
+        if shared is not None:
+            out = tuple(x[:r.n] for x in shared)
+        else:
+            out = r.out_host if r.out_host else _pinned_outputs(r.n, k)
         target.knn_cov_host(r.q_host, k, eps, out=out, stream=stream)
         r.t_done = time.perf_counter() - t0
         r.out_host = out if keep_results else ()
