@@ -87,7 +87,7 @@ __device__ int nearest_within(const Grid& g, float px, float py, float pz, float
                         bpos = pos;
                     }
                 };
-                if (g.occ) for_rows(g, px, py, pz, lx, hx, ly, hy, lz, hz, eta, T, visit);
+                if (g.dstart) for_rows(g, px, py, pz, lx, hx, ly, hy, lz, hz, eta, T, visit);
                 else for_box_points(g, px, py, pz, lx, hx, ly, hy, lz, hz, eta, T, visit);
             }
             if (best != EMPTY_KEY) {

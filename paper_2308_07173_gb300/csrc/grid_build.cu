@@ -514,7 +514,7 @@ cudaError_t count_cells(const float* xyz, int64_t M, const float o[3], float h, 
 
 void pc_free_grid(pc_target_s* t) {
     void* ps[] = {t->table, t->pts, t->xyz, t->cell_keys, t->cell_start, t->status, t->stage,
-                  t->occ, t->rank, t->dstart};
+                  t->dstart};
     for (void* p : ps)
         if (p) cudaFree(p);
     t->table = nullptr;
@@ -522,8 +522,6 @@ void pc_free_grid(pc_target_s* t) {
     t->cell_keys = nullptr;
     t->cell_start = nullptr;
     t->status = nullptr;
-    t->occ = nullptr;
-    t->rank = nullptr;
     t->dstart = nullptr;
     t->stage = nullptr;
     t->stage_bytes = 0;
@@ -648,29 +646,28 @@ pc_status pc_build_grid(const float* xyz, int64_t M, const pc_build_opts& opts, 
                                                     log2cap);
     PC_TRY(cudaGetLastError());
 
-    // 6b. row index: occupancy bitmap over the grid + rank per 32-cell word
+    // 6b. row index: dense cell starts over the grid, built through an
+    // occupancy bitmap and per-word ranks in scratch memory, when they cost
+    // at most eight times the points' copy (else searches visit cells
+    // through the hash)
     const int64_t ngrid = (int64_t)dims[0] * dims[1] * dims[2];
-    int64_t nwords = 0, dense_words = 0;
-    if (ngrid <= ((int64_t)1 << 36)) {
-        nwords = (ngrid + 31) / 32;
-        PC_TRY(cudaMalloc(&t->occ, sizeof(uint32_t) * (size_t)nwords));
-        PC_TRY(cudaMalloc(&t->rank, sizeof(uint32_t) * (size_t)nwords));
+    int64_t dense_words = 0;
+    if (ngrid < ((int64_t)1 << 31) && (ngrid + 1) * 4 <= 8 * 16 * M) {
+        const int64_t nwords = (ngrid + 31) / 32;
+        uint32_t* occ = sc.alloc<uint32_t>(nwords);
+        uint32_t* rank = sc.alloc<uint32_t>(nwords);
         uint32_t* pop = sc.alloc<uint32_t>(nwords);
         uint32_t* tot2 = sc.alloc<uint32_t>(1);
-        if (!pop || !tot2) return pc_from_cuda(sc.err);
-        PC_TRY(cudaMemsetAsync(t->occ, 0, sizeof(uint32_t) * (size_t)nwords, s));
-        k_occ_set<<<grid_for(U, 256), 256, 0, s>>>(t->cell_keys, U, bx, by, dims[0], dims[1], t->occ);
-        k_popc<<<grid_for(nwords, 256), 256, 0, s>>>(t->occ, nwords, pop);
+        if (!occ || !rank || !pop || !tot2) return pc_from_cuda(sc.err);
+        PC_TRY(cudaMemsetAsync(occ, 0, sizeof(uint32_t) * (size_t)nwords, s));
+        k_occ_set<<<grid_for(U, 256), 256, 0, s>>>(t->cell_keys, U, bx, by, dims[0], dims[1], occ);
+        k_popc<<<grid_for(nwords, 256), 256, 0, s>>>(occ, nwords, pop);
         PC_TRY(cudaGetLastError());
-        PC_TRY(scan_exclusive(pop, t->rank, nwords, tot2, sc, s));
-        // dense starts when they cost at most eight times the points' copy
-        if (ngrid < ((int64_t)1 << 31) && (ngrid + 1) * 4 <= 8 * 16 * M) {
-            PC_TRY(cudaMalloc(&t->dstart, sizeof(uint32_t) * (size_t)(ngrid + 1)));
-            k_dstart<<<grid_for(ngrid + 1, 256), 256, 0, s>>>(t->occ, t->rank, t->cell_start, ngrid, U,
-                                                              t->dstart);
-            PC_TRY(cudaGetLastError());
-            dense_words = ngrid + 1;
-        }
+        PC_TRY(scan_exclusive(pop, rank, nwords, tot2, sc, s));
+        PC_TRY(cudaMalloc(&t->dstart, sizeof(uint32_t) * (size_t)(ngrid + 1)));
+        k_dstart<<<grid_for(ngrid + 1, 256), 256, 0, s>>>(occ, rank, t->cell_start, ngrid, U, t->dstart);
+        PC_TRY(cudaGetLastError());
+        dense_words = ngrid + 1;
     }
 
     // 7. float4 copies
@@ -702,14 +699,12 @@ pc_status pc_build_grid(const float* xyz, int64_t M, const pc_build_opts& opts, 
     g.xyz = t->xyz;
     g.cell_keys = t->cell_keys;
     g.cell_start = t->cell_start;
-    g.occ = t->occ;
-    g.rank = t->rank;
     g.dstart = t->dstart;
     g.status = t->status;
     g.stats = reinterpret_cast<unsigned long long*>(reinterpret_cast<char*>(t->status) + 32);
     pc_clear_window(g);
     t->device_bytes = (int64_t)(sizeof(uint4) * t->table_cap + 2 * sizeof(float4) * M +
                                 sizeof(u64) * U + sizeof(uint32_t) * (U + 1) + 64 +
-                                2 * sizeof(uint32_t) * nwords + sizeof(uint32_t) * dense_words);
+                                sizeof(uint32_t) * dense_words);
     return PC_OK;
 }

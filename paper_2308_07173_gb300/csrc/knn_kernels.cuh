@@ -744,7 +744,7 @@ __device__ __forceinline__ float probe_radius(const Grid& g, float qx, float qy,
     const int y0 = max(cy - 1, WIN ? g.wly : 0), y1 = min(cy + 1, WIN ? g.why : g.dimy - 1);
     const int z0 = max(cz - 1, WIN ? g.wlz : 0), z1 = min(cz + 1, WIN ? g.whz : g.dimz - 1);
     uint32_t n = 0;
-    if (g.occ && x0 <= x1)
+    if (g.dstart && x0 <= x1)
         for (int z = z0; z <= z1; ++z)
             for (int y = y0; y <= y1; ++y) n += row_range(g, y, z, x0, x1).y;
     const float cap = 3.0f * g.h;
@@ -829,7 +829,7 @@ __device__ void lane_tile(const Grid& g, const Grid& dg, const float* __restrict
             lz = max(ulz, WIN ? g.wlz : 0); hz = min(uhz, WIN ? g.whz : g.dimz - 1);
             const int64_t ncl = (int64_t)max(hx - lx + 1, 0) * max(hy - ly + 1, 0) * max(hz - lz + 1, 0);
             const int64_t nrows = (int64_t)max(hy - ly + 1, 0) * max(hz - lz + 1, 0);
-            bool big = ncl > 4096 || nrows > 256 || (!g.occ && ncl > 256);
+            bool big = ncl > 4096 || nrows > 256 || (!g.dstart && ncl > 256);
             if (DEL) {
                 const int vlx = cell_of(__fsub_rn(qx, rmax), dg.ox, dg.inv_h);
                 const int vhx = cell_of(__fadd_rn(qx, rmax), dg.ox, dg.inv_h);
@@ -847,7 +847,7 @@ __device__ void lane_tile(const Grid& g, const Grid& dg, const float* __restrict
                 const int64_t dncl =
                     (int64_t)max(dhx - dlx + 1, 0) * max(dhy - dly + 1, 0) * max(dhz - dlz + 1, 0);
                 const int64_t dnrows = (int64_t)max(dhy - dly + 1, 0) * max(dhz - dlz + 1, 0);
-                big = big || dncl > 4096 || dnrows > 256 || (!dg.occ && dncl > 256);
+                big = big || dncl > 4096 || dnrows > 256 || (!dg.dstart && dncl > 256);
             }
             fallback = false;
             if (tau < 0.0f || big) {
@@ -868,10 +868,10 @@ __device__ void lane_tile(const Grid& g, const Grid& dg, const float* __restrict
 #pragma unroll
                     for (int j = 0; j < NRAD; ++j) c[j] += d <= t[j] ? 1 : 0;
                 };
-                if (g.occ) for_rows<WIN>(g, qx, qy, qz, lx, hx, ly, hy, lz, hz, eta, t[NRAD - 1], count);
+                if (g.dstart) for_rows<WIN>(g, qx, qy, qz, lx, hx, ly, hy, lz, hz, eta, t[NRAD - 1], count);
                 else for_box_points<WIN>(g, qx, qy, qz, lx, hx, ly, hy, lz, hz, eta, t[NRAD - 1], count);
                 if (DEL) {
-                    if (dg.occ)
+                    if (dg.dstart)
                         for_rows<WIN>(dg, qx, qy, qz, dlx, dhx, dly, dhy, dlz, dhz, deta, t[NRAD - 1], count);
                     else
                         for_box_points<WIN>(dg, qx, qy, qz, dlx, dhx, dly, dhy, dlz, dhz, deta, t[NRAD - 1],
@@ -918,11 +918,11 @@ __device__ void lane_tile(const Grid& g, const Grid& dg, const float* __restrict
                 ++w;
             }
         };
-        if (g.occ) for_rows<WIN>(g, qx, qy, qz, lx, hx, ly, hy, lz, hz, eta, thr, collect);
+        if (g.dstart) for_rows<WIN>(g, qx, qy, qz, lx, hx, ly, hy, lz, hz, eta, thr, collect);
         else for_box_points<WIN>(g, qx, qy, qz, lx, hx, ly, hy, lz, hz, eta, thr, collect);
         if (DEL) {
             auto collect_d = [&](uint32_t pos, const float4 p) { collect(pos | DTAG, p); };
-            if (dg.occ) for_rows<WIN>(dg, qx, qy, qz, dlx, dhx, dly, dhy, dlz, dhz, deta, thr, collect_d);
+            if (dg.dstart) for_rows<WIN>(dg, qx, qy, qz, dlx, dhx, dly, dhy, dlz, dhz, deta, thr, collect_d);
             else for_box_points<WIN>(dg, qx, qy, qz, dlx, dhx, dly, dhy, dlz, dhz, deta, thr, collect_d);
         }
     }

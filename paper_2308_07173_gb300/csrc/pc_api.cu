@@ -739,8 +739,6 @@ pc_status pc_target_compact(pc_target t, pc_stream s) {
     t->xyz = n->xyz;
     t->cell_keys = n->cell_keys;
     t->cell_start = n->cell_start;
-    t->occ = n->occ;
-    t->rank = n->rank;
     t->dstart = n->dstart;
     t->status = n->status;
     delete n;  // its buffers now belong to t

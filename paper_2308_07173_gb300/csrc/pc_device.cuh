@@ -40,16 +40,11 @@ struct Grid {
     const float4* xyz;      // caller order: (x, y, z, 0)
     const unsigned long long* cell_keys;  // occupied cell keys, ascending [ncells]
     const uint32_t* cell_start;           // [ncells + 1] into pts
-    // Row index (null when the grid is too large for it): bit L of occ is
-    // set when cell L = cx + dimx (cy + dimy cz) is occupied, rank[w] counts
-    // the set bits in words before w.  Occupied cells are ordered by L, so a
-    // run of cells along x maps to one contiguous range of pts.
-    const uint32_t* occ;
-    const uint32_t* rank;
-    // Dense starts (null when the grid is too large for them): dstart[L] is
-    // the position in pts of the first point of the occupied cells with
-    // linear index >= L, for L in [0, dimx dimy dimz]; a row's run of cells
-    // is then one pair of loads, without the bitmap.
+    // Row index (null when the grid is too large for it): dstart[L] is the
+    // position in pts of the first point of the occupied cells with linear
+    // index >= L, L = cx + dimx (cy + dimy cz) in [0, dimx dimy dimz].
+    // Occupied cells are ordered by L, so a run of cells along x is one
+    // contiguous range of pts, read with one pair of loads.
     const uint32_t* dstart;
     int* status;
     unsigned long long* stats;  // [0] queries, [1] warp-search fallbacks, [2] exhaustive scans,
@@ -104,35 +99,12 @@ __device__ __forceinline__ uint2 lookup_cell(const Grid& g, unsigned long long k
     return make_uint2(0u, 0u);
 }
 
-// Ranks (u0, u1) of the occupied cells x0..x1 (x0 <= x1) of row (cy, cz)
-// among all occupied cells, through the row index: the row's points are
-// pts[cell_start[u0], cell_start[u1]).
-__device__ __forceinline__ uint2 row_cell_ranks(const Grid& g, int cy, int cz, int x0, int x1) {
-    const int64_t base = (int64_t)g.dimx * ((int64_t)cy + (int64_t)g.dimy * cz);
-    const int64_t L0 = base + x0, L1 = base + x1;
-    const int64_t w0 = L0 >> 5, w1 = L1 >> 5;
-    const uint32_t o0 = __ldg(&g.occ[w0]);
-    const uint32_t r0 = __ldg(&g.rank[w0]);
-    const uint32_t u0 = r0 + __popc(o0 & ((1u << (uint32_t)(L0 & 31)) - 1u));
-    const uint32_t b1 = (uint32_t)(L1 & 31);
-    const uint32_t upto = b1 == 31u ? 0xffffffffu : ((2u << b1) - 1u);
-    const uint32_t u1 = (w1 == w0) ? r0 + __popc(o0 & upto)
-                                   : __ldg(&g.rank[w1]) + __popc(__ldg(&g.occ[w1]) & upto);
-    return make_uint2(u0, u1);
-}
-
 // Points of the occupied cells x0..x1 (x0 <= x1) of row (cy, cz) as one
 // range (start, count) of pts, through the row index.
 __device__ __forceinline__ uint2 row_range(const Grid& g, int cy, int cz, int x0, int x1) {
-    if (g.dstart) {
-        const int64_t base = (int64_t)g.dimx * ((int64_t)cy + (int64_t)g.dimy * cz);
-        const uint32_t s = __ldg(&g.dstart[base + x0]);
-        return make_uint2(s, __ldg(&g.dstart[base + x1 + 1]) - s);
-    }
-    const uint2 u = row_cell_ranks(g, cy, cz, x0, x1);
-    if (u.y == u.x) return make_uint2(0u, 0u);
-    const uint32_t s = __ldg(&g.cell_start[u.x]);
-    return make_uint2(s, __ldg(&g.cell_start[u.y]) - s);
+    const int64_t base = (int64_t)g.dimx * ((int64_t)cy + (int64_t)g.dimy * cz);
+    const uint32_t s = __ldg(&g.dstart[base + x0]);
+    return make_uint2(s, __ldg(&g.dstart[base + x1 + 1]) - s);
 }
 
 // The pinned binary32 squared distance: fmaf(dz,dz, fmaf(dy,dy, dx*dx)).

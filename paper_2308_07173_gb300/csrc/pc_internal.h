@@ -48,8 +48,6 @@ struct pc_target_s {
     float4* xyz;
     unsigned long long* cell_keys;
     uint32_t* cell_start;
-    uint32_t* occ;
-    uint32_t* rank;
     uint32_t* dstart;
     int* status;  // 64 bytes: status word, then 4 u64 statistics counters at +32
     // staging for pc_knn_cov_host, grown on demand
