@@ -7,8 +7,9 @@ covariance + plane regularisation) with the map grid resident.  The timed
 value is device time (CUDA events on the launching stream) with inputs in
 HBM and L2 flushed (a 256 MB write) before every timed step, outside the
 events.  `e2e` repeats the step through the host-buffer entry
-pc_knn_cov_host: pinned-host scan in, idx/d2/cov back to pinned host memory,
-copies inside the timed region.
+pc_knn_cov_host with page-locked host buffers (the search reads the scan
+and writes idx/d2/cov in host memory itself), every host<->device transfer
+inside the timed region.
 
 Multi-GPU (torchrun): every rank processes its own scan per step against
 its own copy of the map -- queries shard with no data-path collective
@@ -490,6 +491,8 @@ def run_c2(args):
             "l2_traffic": l2,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 12 * N,
                     "d2h_bytes_per_step": N * (8 * K_NN + 24), "step": "one scan through pc_knn_cov_host",
+                    "path": "page-locked buffers: q read and idx/d2/cov written in place by the search "
+                            "(whole-line block writes per warp); `copies` times the staged-copy path's parts",
                     "copies": copy_probe},
             "issue_roofline": issue_roofline(ms_per_scan, clk,
                                              torch.cuda.get_device_properties(dev).multi_processor_count),

@@ -257,11 +257,18 @@ PC_API pc_status pc_target_compact(pc_target t, pc_stream s);
 PC_API pc_status pc_knn_cov(pc_target t, const float *q_dev, int64_t N, int k, float eps,
                      int32_t *idx_dev, float *d2_dev, float *cov_dev, pc_stream s);
 
-/* pc_knn_cov from HOST buffers (pinned or pageable): copies q in, runs, copies
- * idx/d2/cov out, and synchronises `s` before returning.  Device staging
- * buffers are kept in the handle and grown on demand (PC_ERR_OOM if that
- * fails).  Device-side conditions are returned directly (no separate
- * pc_sync_status needed). */
+/* pc_knn_cov from HOST buffers (pinned or pageable), synchronising `s`
+ * before returning; results identical to pc_knn_cov.  When idx, d2 and cov
+ * are all page-locked and mapped into the device's address space
+ * (cudaHostAlloc, cudaHostRegister, torch pin_memory), k <= 32 and the
+ * target has no appended points, the search writes them in place: each
+ * warp stages its tile's rows in shared memory and writes them as whole
+ * lines, so the transfer runs during the search; a page-locked q is then
+ * also read in place.  Otherwise q is copied in and idx/d2/cov copied out
+ * through device staging buffers kept in the handle and grown on demand
+ * (PC_ERR_OOM if that fails).  Device-side conditions are returned
+ * directly (no separate pc_sync_status needed); rows are written as by
+ * pc_knn_cov even then. */
 PC_API pc_status pc_knn_cov_host(pc_target t, const float *q_host, int64_t N, int k, float eps,
                           int32_t *idx_host, float *d2_host, float *cov_host, pc_stream s);
 

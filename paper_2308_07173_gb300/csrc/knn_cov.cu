@@ -71,16 +71,16 @@ int clamp_warps(int w) { return w <= 0 ? 4 : (w > 8 ? 8 : w); }
 
 // Calls f(kernel) with the search kernel for (mode, with_cov, windowed).
 template <bool BATCH, typename F>
-cudaError_t with_kernel(int mode, bool with_cov, bool windowed, F&& f) {
-    void* kern = windowed ? pc_knn_kernel_win(mode, with_cov, BATCH)
-                          : knn_kernel<false>(mode, with_cov, BATCH);
+cudaError_t with_kernel(int mode, bool with_cov, bool windowed, F&& f, bool stage = false) {
+    void* kern = windowed ? pc_knn_kernel_win(mode, with_cov, BATCH, stage)
+                          : knn_kernel<false>(mode, with_cov, BATCH, stage);
     return f(kern);
 }
 
 }  // namespace
 
 cudaError_t pc_launch_knn(const pc_target_s* t, const float* q, int64_t N, int k, float eps,
-                          int32_t* idx, float* d2, float* cov, float rho0, cudaStream_t s) {
+                          int32_t* idx, float* d2, float* cov, float rho0, cudaStream_t s, bool stage) {
     if (N == 0) return cudaSuccess;
     cudaError_t e = ensure_attrs();
     if (e != cudaSuccess) return e;
@@ -88,19 +88,21 @@ cudaError_t pc_launch_knn(const pc_target_s* t, const float* q, int64_t N, int k
     const int warps = clamp_warps(t->tune.warps);
     // the covariance (plain, or weighted by the target's kernel descriptor)
     // is fused into the search
-    TileArgs a{k, eps, t->tune.rho_scale > 0 ? t->tune.rho_scale : 0.9f, t->tune.order == 0 ? 1 : 0, t->ck,
-               pc_probe_c(t)};
     const bool with_cov = cov != nullptr;
     const int mode = target_mode(t, k);
-    const size_t smem = (size_t)warps * warp_smem_bytes(mode);
+    stage = stage && mode < 2 && with_cov;  // the warp path writes its rows directly
+    TileArgs a{k, eps, t->tune.rho_scale > 0 ? t->tune.rho_scale : 0.9f, t->tune.order == 0 ? 1 : 0, t->ck,
+               pc_probe_c(t)};
+    const size_t smem = (size_t)warps * warp_bytes(mode, stage, k);
     const int64_t tiles = (N + tile - 1) / tile;
     const int64_t blocks = (tiles + warps - 1) / warps;
     Grid g = t->g;
     float* covp = with_cov ? cov : nullptr;
     void* args[] = {&g, (void*)&q, (void*)&N, (void*)&tile, &a, &rho0, &idx, &d2, &covp};
-    return with_kernel<false>(mode, with_cov, g.windowed != 0, [&](void* kern) {
-        return cudaLaunchKernel(kern, dim3((unsigned)blocks), dim3(warps * 32), args, smem, s);
-    });
+    return with_kernel<false>(
+        mode, with_cov, g.windowed != 0,
+        [&](void* kern) { return cudaLaunchKernel(kern, dim3((unsigned)blocks), dim3(warps * 32), args, smem, s); },
+        stage);
 }
 
 // The union search (a target with appended points): the same launch shape
@@ -112,10 +114,10 @@ cudaError_t pc_launch_knn_union(const pc_target_s* t, const float* q, int64_t N,
     if (e != cudaSuccess) return e;
     const int tile = clamp_tile(t->tune.tile);
     const int warps = clamp_warps(t->tune.warps);
-    TileArgs a{k, eps, t->tune.rho_scale > 0 ? t->tune.rho_scale : 0.9f, t->tune.order == 0 ? 1 : 0, t->ck,
-               pc_probe_c(t)};
     const bool with_cov = cov != nullptr;
     const int mode = target_mode(t, k);
+    TileArgs a{k, eps, t->tune.rho_scale > 0 ? t->tune.rho_scale : 0.9f, t->tune.order == 0 ? 1 : 0, t->ck,
+               pc_probe_c(t)};
     const size_t smem = (size_t)warps * warp_smem_bytes(mode);
     const int64_t tiles = (N + tile - 1) / tile;
     const int64_t blocks = (tiles + warps - 1) / warps;

@@ -653,6 +653,26 @@ __host__ __device__ __forceinline__ int search_mode(int k) { return k <= 24 ? 0 
 __host__ __device__ __forceinline__ size_t warp_smem_bytes(int mode) {
     return 64 * sizeof(u64) + (size_t)lane_cap(mode) * 32 * sizeof(uint32_t);
 }
+// Staging area of a warp whose outputs go to host memory: the tile's idx
+// rows, d2 rows and covariance rows, each laid out as in the output arrays.
+__host__ __device__ __forceinline__ size_t stage_bytes(int k) { return (size_t)32 * (2 * k + 6) * sizeof(float); }
+__host__ __device__ __forceinline__ size_t warp_bytes(int mode, bool stage, int k) {
+    return warp_smem_bytes(mode) + (stage ? stage_bytes(k) : 0);
+}
+
+// Copies n words from shared memory to global (or host-mapped) memory with
+// the whole warp: 16-byte vectors when both ends allow it, so each store
+// instruction writes 512 contiguous bytes.
+__device__ __forceinline__ void warp_copy_out(uint32_t* __restrict__ dst, const uint32_t* src, int n, int lane) {
+    int done = 0;
+    if (((reinterpret_cast<uintptr_t>(dst) | reinterpret_cast<uintptr_t>(src)) & 15) == 0) {
+        const int n4 = n >> 2;
+        for (int i = lane; i < n4; i += 32)
+            reinterpret_cast<uint4*>(dst)[i] = reinterpret_cast<const uint4*>(src)[i];
+        done = n4 << 2;
+    }
+    for (int i = done + lane; i < n; i += 32) dst[i] = src[i];
+}
 
 __device__ __forceinline__ void cas32(uint32_t& a, uint32_t& b) {
     const uint32_t lo = min(a, b), hi = max(a, b);
@@ -769,16 +789,21 @@ __device__ __forceinline__ float probe_radius(const Grid& g, float qx, float qy,
 // appended points (point j of dg is g.m + j): both grids' boxes of the trial
 // radius are counted and collected in the same passes, filtered by the
 // smaller of their certified taus, and list entries from dg carry DTAG.
-template <int CAP, bool COV, bool WIN, bool DEL>
+template <int CAP, bool COV, bool WIN, bool DEL, bool STG>
 __device__ void lane_tile(const Grid& g, const Grid& dg, const float* __restrict__ q, int64_t n0, int cnt,
                           const TileArgs& a, float rho0, int32_t* __restrict__ idx,
                           float* __restrict__ d2, float* __restrict__ cov, u64* pend,
-                          uint32_t* posl, int lane) {
+                          uint32_t* posl, uint32_t* stg, int lane) {
     constexpr int NRAD = Ladder<CAP>::N;
     auto rad_mul = [](int jj) { return Ladder<CAP>::mul(jj); };
     const int k = a.k;
     const bool active = lane < cnt;
     const int64_t n = n0 + lane;
+    // With STG the rows go to the warp's staging area (laid out as in the
+    // output arrays) and are copied out as one block per tile.
+    int32_t* const si = reinterpret_cast<int32_t*>(stg);
+    float* const sd = reinterpret_cast<float*>(stg + 32 * k);
+    float* const sc = reinterpret_cast<float*>(stg + 64 * k);
     float qx = 0.0f, qy = 0.0f, qz = 0.0f;
     if (active) {
         qx = __ldg(q + 3 * n);
@@ -963,6 +988,8 @@ __device__ void lane_tile(const Grid& g, const Grid& dg, const float* __restrict
         amb = swapped;
     }
     if (m > 0) {
+        int32_t* const irow = STG ? si + lane * k : idx + n * k;
+        float* const drow = STG ? sd + lane * k : d2 + n * k;
         // rank-ordered positions, rewritten in place into the list's first k slots
         uint32_t P[32];
 #pragma unroll
@@ -971,7 +998,8 @@ __device__ void lane_tile(const Grid& g, const Grid& dg, const float* __restrict
         // Each lane writes its own row, so every store instruction touches
         // 32 rows; a row of 4j (2j) entries on a 16- (8-) byte aligned base is
         // whole vectors, which takes a quarter (half) of the instructions.
-        const uintptr_t ab = reinterpret_cast<uintptr_t>(idx) | reinterpret_cast<uintptr_t>(d2);
+        const uintptr_t ab = STG ? reinterpret_cast<uintptr_t>(stg)
+                                 : reinterpret_cast<uintptr_t>(idx) | reinterpret_cast<uintptr_t>(d2);
         const int vw = ((k & 3) == 0 && (ab & 15) == 0) ? 4 : (((k & 1) == 0 && (ab & 7) == 0) ? 2 : 1);
         auto entry = [&](int r, int& iv, float& dv) {
             posl[r * 32 + lane] = P[r];
@@ -989,8 +1017,8 @@ __device__ void lane_tile(const Grid& g, const Grid& dg, const float* __restrict
                     entry(r + 1, iv.y, dv.y);
                     entry(r + 2, iv.z, dv.z);
                     entry(r + 3, iv.w, dv.w);
-                    *reinterpret_cast<int4*>(idx + n * k + r) = iv;
-                    *reinterpret_cast<float4*>(d2 + n * k + r) = dv;
+                    *reinterpret_cast<int4*>(irow + r) = iv;
+                    *reinterpret_cast<float4*>(drow + r) = dv;
                 }
         } else if (vw == 2) {
 #pragma unroll
@@ -1000,8 +1028,8 @@ __device__ void lane_tile(const Grid& g, const Grid& dg, const float* __restrict
                     float2 dv;
                     entry(r, iv.x, dv.x);
                     entry(r + 1, iv.y, dv.y);
-                    *reinterpret_cast<int2*>(idx + n * k + r) = iv;
-                    *reinterpret_cast<float2*>(d2 + n * k + r) = dv;
+                    *reinterpret_cast<int2*>(irow + r) = iv;
+                    *reinterpret_cast<float2*>(drow + r) = dv;
                 }
         } else {
 #pragma unroll
@@ -1010,14 +1038,16 @@ __device__ void lane_tile(const Grid& g, const Grid& dg, const float* __restrict
                     int iv;
                     float dv;
                     entry(r, iv, dv);
-                    idx[n * k + r] = iv;
-                    d2[n * k + r] = dv;
+                    irow[r] = iv;
+                    drow[r] = dv;
                 }
         }
     } else if (active && !finite) {
+        int32_t* const irow = STG ? si + lane * k : idx + n * k;
+        float* const drow = STG ? sd + lane * k : d2 + n * k;
         for (int r = 0; r < k; ++r) {
-            idx[n * k + r] = -1;
-            d2[n * k + r] = INFINITY;
+            irow[r] = -1;
+            drow[r] = INFINITY;
         }
         atomicOr(g.status, ST_NONFINITE);
     }
@@ -1041,18 +1071,30 @@ __device__ void lane_tile(const Grid& g, const Grid& dg, const float* __restrict
         if (!ok && lane == 0) atomicOr(g.status, sr == SEARCH_SHORT ? ST_SHORT : ST_SEARCH_LIMIT);
         const int64_t nf = n0 + f;
         if (lane < k) {
-            idx[nf * k + lane] = ok ? (int32_t)(uint32_t)S.L[0] : -1;
-            d2[nf * k + lane] = ok ? __uint_as_float((uint32_t)(S.L[0] >> 32)) : INFINITY;
+            int32_t* const fi = STG ? si + f * k : idx + nf * k;
+            float* const fd = STG ? sd + f * k : d2 + nf * k;
+            fi[lane] = ok ? (int32_t)(uint32_t)S.L[0] : -1;
+            fd[lane] = ok ? __uint_as_float((uint32_t)(S.L[0] >> 32)) : INFINITY;
         }
+    }
+    if (STG) {
+        __syncwarp();  // the staged rows of every lane, then one block per array
+        warp_copy_out(reinterpret_cast<uint32_t*>(idx + n0 * k), stg, cnt * k, lane);
+        warp_copy_out(reinterpret_cast<uint32_t*>(d2 + n0 * k), stg + 32 * k, cnt * k, lane);
     }
     if (COV && cov != nullptr) {
         __syncwarp();  // orders the idx rows written by other lanes
+        float* const crow = STG ? sc + 6 * lane : cov + 6 * n;
         if (m > 0) {  // neighbours straight from the cell-sorted copy, in rank order
             auto get = [&](int j) { return pt_at<DEL>(g, dg, posl[j * 32 + lane]); };
-            if (a.ck.type != 0) weighted_core(get, a.ck, qx, qy, qz, k, a.eps, cov + 6 * n);
-            else cov_core(get, k, a.eps, cov + 6 * n);
+            if (a.ck.type != 0) weighted_core(get, a.ck, qx, qy, qz, k, a.eps, crow);
+            else cov_core(get, k, a.eps, crow);
         } else if (active) {
-            cov_row_any<DEL>(g, dg, idx + n * k, k, a, qx, qy, qz, cov + 6 * n);
+            cov_row_any<DEL>(g, dg, STG ? si + lane * k : idx + n * k, k, a, qx, qy, qz, crow);
+        }
+        if (STG) {
+            __syncwarp();
+            warp_copy_out(reinterpret_cast<uint32_t*>(cov + 6 * n0), stg + 64 * k, cnt * 6, lane);
         }
     }
     __syncwarp();
@@ -1107,7 +1149,7 @@ __device__ void warp_tile(const Grid& g, const Grid& dg, const float* __restrict
     }
 }
 
-template <int MODE, bool COV, bool WIN, bool DEL = false>
+template <int MODE, bool COV, bool WIN, bool DEL = false, bool STG = false>
 __device__ __forceinline__ void process_tile(const Grid& g, const Grid& dg, const float* __restrict__ q, int64_t n0,
                                              int cnt, const TileArgs& a, float rho0,
                                              int32_t* __restrict__ idx, float* __restrict__ d2,
@@ -1115,15 +1157,16 @@ __device__ __forceinline__ void process_tile(const Grid& g, const Grid& dg, cons
                                              int lane) {
     u64* pend = reinterpret_cast<u64*>(wsmem);
     uint32_t* posl = reinterpret_cast<uint32_t*>(wsmem + 64 * sizeof(u64));
+    uint32_t* stg = STG ? reinterpret_cast<uint32_t*>(wsmem + warp_smem_bytes(MODE)) : nullptr;
     if (MODE == 0)
-        lane_tile<32, COV, WIN, DEL>(g, dg, q, n0, cnt, a, rho0, idx, d2, cov, pend, posl, lane);
+        lane_tile<32, COV, WIN, DEL, STG>(g, dg, q, n0, cnt, a, rho0, idx, d2, cov, pend, posl, stg, lane);
     else if (MODE == 1)
-        lane_tile<64, COV, WIN, DEL>(g, dg, q, n0, cnt, a, rho0, idx, d2, cov, pend, posl, lane);
+        lane_tile<64, COV, WIN, DEL, STG>(g, dg, q, n0, cnt, a, rho0, idx, d2, cov, pend, posl, stg, lane);
     else
         warp_tile<COV, DEL>(g, dg, q, n0, cnt, a, rho0, idx, d2, cov, pend, lane);
 }
 
-template <int MODE, bool COV, bool WIN>
+template <int MODE, bool COV, bool WIN, bool STG = false>
 __global__ void __launch_bounds__(256, 2) k_knn(Grid g, const float* __restrict__ q, int64_t N,
                                              int tile, TileArgs a, float rho0,
                                              int32_t* __restrict__ idx, float* __restrict__ d2,
@@ -1141,8 +1184,8 @@ __global__ void __launch_bounds__(256, 2) k_knn(Grid g, const float* __restrict_
     const int64_t t = a.last_first ? tiles - 1 - w : w;
     const int64_t n0 = t * tile;
     const int cnt = (int)min((int64_t)tile, N - n0);
-    process_tile<MODE, COV, WIN>(g, g, q, n0, cnt, a, rho0, idx, d2, cov,
-                                 smem + (size_t)warp * warp_smem_bytes(MODE), lane);
+    process_tile<MODE, COV, WIN, false, STG>(g, g, q, n0, cnt, a, rho0, idx, d2, cov,
+                                             smem + (size_t)warp * warp_bytes(MODE, STG, a.k), lane);
 }
 
 // Batched form: one warp per (scan, tile) item of the scans' prefix-summed
@@ -1210,7 +1253,10 @@ cudaError_t allow_smem(K kern) {
 
 // The search kernel for (mode, covariance, batched) of this window variant.
 template <bool WIN>
-void* knn_kernel(int mode, bool with_cov, bool batch) {
+void* knn_kernel(int mode, bool with_cov, bool batch, bool stage = false) {
+    // outputs in host memory: the staged lane-path kernels (with covariance)
+    if (stage && !batch && with_cov && mode < 2)
+        return mode == 0 ? (void*)k_knn<0, true, WIN, true> : (void*)k_knn<1, true, WIN, true>;
 #define PC_PICK(M, C) (batch ? (void*)k_knn_batch<M, C, WIN> : (void*)k_knn<M, C, WIN>)
     switch (mode * 2 + (with_cov ? 1 : 0)) {
         case 0: return PC_PICK(0, false);
@@ -1254,6 +1300,8 @@ cudaError_t allow_all_smem() {
         for (int c = 0; c < 2; ++c)
             for (int b = 0; b < 2; ++b)
                 if ((e = allow_smem(knn_kernel<WIN>(mode, c != 0, b != 0))) != cudaSuccess) return e;
+    for (int mode = 0; mode < 2; ++mode)
+        if ((e = allow_smem(knn_kernel<WIN>(mode, true, false, true))) != cudaSuccess) return e;
     return cudaSuccess;
 }
 

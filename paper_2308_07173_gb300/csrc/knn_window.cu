@@ -3,8 +3,8 @@
 // cells test each point against the window box.
 #include "knn_kernels.cuh"
 
-void* pc_knn_kernel_win(int mode, bool with_cov, bool batch) {
-    return knn_kernel<true>(mode, with_cov, batch);
+void* pc_knn_kernel_win(int mode, bool with_cov, bool batch, bool stage) {
+    return knn_kernel<true>(mode, with_cov, batch, stage);
 }
 
 cudaError_t pc_knn_win_attrs() { return allow_all_smem<true>(); }

@@ -196,9 +196,21 @@ static pc_status build_target_internal(const float* xyz, int64_t M, const pc_bui
 // The search over the target as it stands: its grid, or its grid and the
 // delta grid of appended points searched as one map.
 static pc_status launch_search(pc_target_s* t, const float* q, int64_t N, int k, float eps, int32_t* idx,
-                               float* d2, float* cov, cudaStream_t st) {
-    if (!t->delta) return pc_from_cuda(pc_launch_knn(t, q, N, k, eps, idx, d2, cov, pc_rho0(t, k), st));
+                               float* d2, float* cov, cudaStream_t st, bool stage = false) {
+    if (!t->delta) return pc_from_cuda(pc_launch_knn(t, q, N, k, eps, idx, d2, cov, pc_rho0(t, k), st, stage));
     return pc_from_cuda(pc_launch_knn_union(t, q, N, k, eps, idx, d2, cov, pc_rho0(t, k), st));
+}
+
+// The device address of page-locked host memory mapped into the device's
+// address space (cudaHostAlloc, cudaHostRegister, torch pin_memory), or
+// null for any other pointer.
+static void* mapped_host(const void* p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
 }
 
 static void free_delta(pc_target_s* t) {
@@ -365,6 +377,27 @@ pc_status pc_knn_cov_host(pc_target t, const float* q_host, int64_t N, int k, fl
     if (N == 0) return PC_OK;
     if (!q_host || !idx_host || !d2_host || !cov_host) return PC_ERR_INVALID_ARG;
     DeviceGuard dg(t->device);
+    cudaStream_t st = (cudaStream_t)s;
+    // Page-locked outputs (k <= 32, no appended points): the search writes
+    // them in place, each warp's rows as one block, so the transfer runs
+    // during the search; a page-locked q is read in place too.
+    void* const mi = (k <= 32 && !t->delta) ? mapped_host(idx_host) : nullptr;
+    void* const md = mi ? mapped_host(d2_host) : nullptr;
+    void* const mc = md ? mapped_host(cov_host) : nullptr;
+    if (mc) {
+        const float* q = static_cast<const float*>(mapped_host(q_host));
+        if (!q) {
+            if ((r = ensure_stage(t, align256(sizeof(float) * 3 * N))) != PC_OK) return r;
+            float* qs = static_cast<float*>(t->stage);
+            const cudaError_t e = cudaMemcpyAsync(qs, q_host, sizeof(float) * 3 * N, cudaMemcpyHostToDevice, st);
+            if (e != cudaSuccess) return pc_from_cuda(e);
+            q = qs;
+        }
+        r = launch_search(t, q, N, k, eps, static_cast<int32_t*>(mi), static_cast<float*>(md),
+                          static_cast<float*>(mc), st, true);
+        if (r != PC_OK) return r;
+        return read_and_clear_status(t, st);
+    }
     const size_t bq = align256(sizeof(float) * 3 * N), bi = align256(sizeof(int32_t) * N * k),
                  bd = align256(sizeof(float) * N * k), bc = align256(sizeof(float) * 6 * N);
     if ((r = ensure_stage(t, bq + bi + bd + bc)) != PC_OK) return r;
@@ -373,7 +406,6 @@ pc_status pc_knn_cov_host(pc_target t, const float* q_host, int64_t N, int k, fl
     int32_t* idx = reinterpret_cast<int32_t*>(base + bq);
     float* d2 = reinterpret_cast<float*>(base + bq + bi);
     float* cov = reinterpret_cast<float*>(base + bq + bi + bd);
-    cudaStream_t st = (cudaStream_t)s;
     cudaError_t e = cudaMemcpyAsync(q, q_host, sizeof(float) * 3 * N, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) {
         r = launch_search(t, q, N, k, eps, idx, d2, cov, st);

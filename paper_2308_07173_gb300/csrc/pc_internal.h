@@ -111,12 +111,14 @@ cudaError_t pc_scan_exclusive(const uint32_t* in, uint32_t* out, int64_t n, uint
                               uint32_t* temp, cudaStream_t s);
 
 // knn_window.cu: the window variant of the search kernels
-void* pc_knn_kernel_win(int mode, bool with_cov, bool batch);
+void* pc_knn_kernel_win(int mode, bool with_cov, bool batch, bool stage = false);
 cudaError_t pc_knn_win_attrs();
 
-// knn_cov.cu
+// knn_cov.cu.  stage: the outputs are host-mapped memory; each warp stages
+// its tile's rows in shared memory and writes them as whole blocks (lane
+// path with covariance; the warp path, k > 32, writes its rows directly).
 cudaError_t pc_launch_knn(const pc_target_s* t, const float* q, int64_t N, int k, float eps,
-                          int32_t* idx, float* d2, float* cov, float rho0, cudaStream_t s);
+                          int32_t* idx, float* d2, float* cov, float rho0, cudaStream_t s, bool stage = false);
 cudaError_t pc_launch_knn_union(const pc_target_s* t, const float* q, int64_t N, int k, float eps,
                                 int32_t* idx, float* d2, float* cov, float rho0, cudaStream_t s);
 // Opts the search kernels into large shared memory on the current device
