@@ -648,7 +648,7 @@ def measure_c4(duration: float, speeds, map_points: int = 5_000_000, warm_scans:
     tuned = autotune.lookup(autotune.default_cache(), K_NN, map_points, 0)
     t = autotune.apply(md, tuned) if tuned else pc.Target(md)
     serve.prepare(reqs)
-    srv = serve.Server(t, K_NN, EPS, hbm_budget=2 << 30, max_step_scans=16, slots=3)
+    srv = serve.Server(t, K_NN, EPS, hbm_budget=2 << 30, max_step_scans=16, slots=3, in_place=True)
     warm = serve.requests_from_arrivals(arr[:warm_scans])
     serve.prepare(warm)
     srv.serve(warm, speed=1e6)
@@ -656,7 +656,9 @@ def measure_c4(duration: float, speeds, map_points: int = 5_000_000, warm_scans:
     out = {"workload": f"c4_24lidars_20hz_poisson_map{map_points // 1_000_000}M_k20",
            "arrival_seconds": duration, "scans": len(reqs), "points": npts,
            "offered_points_per_s_at_1x": npts / duration, "hbm_budget_bytes": 2 << 30,
-           "max_step_scans": 16, "slots": 3, "tuned": tuned or "defaults (no cached configuration)"}
+           "max_step_scans": 16, "slots": 3, "tuned": tuned or "defaults (no cached configuration)",
+           "io": "both forms read the page-locked scans and write page-locked results in place "
+                 "(served: one batched launch per step; per-scan: pc_knn_cov_host per scan)"}
     for name, speed in speeds:
         # host-timed latencies: each rate is replayed `repeats` times, served
         # and per-scan in alternating order, and the medians over the replays

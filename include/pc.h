@@ -122,7 +122,14 @@ typedef struct {
                             (its counting and collecting passes together) */
 } pc_stats;
 
-/* One scan of a batch: device pointers, caller-owned. */
+/* One scan of a batch, caller-owned: device memory, or page-locked host
+ * memory mapped into the device's address space (cudaHostAlloc,
+ * cudaHostRegister, torch pin_memory).  When any scan's idx, d2 or cov is
+ * such host memory, the batch runs the staged kernel: each warp writes its
+ * tile's rows as whole blocks, so the results reach host memory during the
+ * search with no copy (for k <= 32; the warp path, k > 32, writes its rows
+ * directly).  Results are identical either way.  Any other pointer returns
+ * PC_ERR_BAD_POINTER. */
 typedef struct {
     const float *q_dev; /* [n,3] */
     int64_t n;
@@ -326,7 +333,7 @@ PC_API pc_status pc_batch_run_scratch(pc_target t, const pc_scan *scans, int n_s
  * one file-scope device array sized for PC_NOALLOC_MAX_SCANS scans (about
  * 12 KB), which every GPU that loads the library keeps until the process
  * exits.  The caller still passes the target, and the inputs and outputs in
- * `scans` (device pointers, as for pc_batch_plan).
+ * `scans` (as for pc_batch_plan).
  *  - n_scans < 1 or > PC_NOALLOC_MAX_SCANS returns PC_ERR_INVALID_ARG and
  *    launches nothing; other argument errors are those of pc_batch_plan.
  *  - The first call on a device looks up the array's device address (once

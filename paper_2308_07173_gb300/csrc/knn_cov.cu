@@ -143,7 +143,7 @@ cudaError_t pc_launch_cov(const pc_target_s* t, const int32_t* idx, int64_t N, i
 cudaError_t pc_launch_knn_batch(const pc_target_s* t, const Grid& gv, const CovKernel& ck,
                                 const ScanDesc* scans_dev, int nscans, int64_t max_n,
                                 int64_t total_tiles, int tile, int warps, int k, float eps,
-                                bool with_cov, float rho0, cudaStream_t s) {
+                                bool with_cov, float rho0, cudaStream_t s, bool stage) {
     if (total_tiles == 0) return cudaSuccess;
     cudaError_t e = ensure_attrs();
     if (e != cudaSuccess) return e;
@@ -152,10 +152,12 @@ cudaError_t pc_launch_knn_batch(const pc_target_s* t, const Grid& gv, const CovK
     const int64_t blocks = (total_tiles + warps - 1) / warps;
     if (blocks > 0x7fffffff) return cudaErrorInvalidValue;
     const int mode = target_mode(t, k);
-    const size_t smem = (size_t)warps * warp_smem_bytes(mode);
+    stage = stage && mode < 2;  // the warp path writes its rows directly
+    const size_t smem = (size_t)warps * warp_bytes(mode, stage, k);
     Grid g = gv;
     void* args[] = {&g, (void*)&scans_dev, &nscans, &total_tiles, &tile, &a, &rho0};
-    return with_kernel<true>(mode, with_cov, g.windowed != 0, [&](void* kern) {
-        return cudaLaunchKernel(kern, dim3((unsigned)blocks), dim3(warps * 32), args, smem, s);
-    });
+    return with_kernel<true>(
+        mode, with_cov, g.windowed != 0,
+        [&](void* kern) { return cudaLaunchKernel(kern, dim3((unsigned)blocks), dim3(warps * 32), args, smem, s); },
+        stage);
 }

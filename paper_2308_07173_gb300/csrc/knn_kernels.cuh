@@ -1196,7 +1196,7 @@ __global__ void __launch_bounds__(256, 2) k_knn(Grid g, const float* __restrict_
 // state the kernel keeps k_knn's registers (a persistent version spilled at
 // the 128-register cap and ran 23 % slower than one launch over the same
 // queries concatenated).
-template <int MODE, bool COV, bool WIN>
+template <int MODE, bool COV, bool WIN, bool STG = false>
 __global__ void __launch_bounds__(256, 2) k_knn_batch(Grid g, const ScanDesc* __restrict__ scans,
                                                    int nscans, int64_t total_tiles, int tile,
                                                    TileArgs a, float rho0) {
@@ -1214,8 +1214,8 @@ __global__ void __launch_bounds__(256, 2) k_knn_batch(Grid g, const ScanDesc* __
     const ScanDesc sd = scans[lo];
     const int64_t n0 = (item - sd.tile0) * tile;
     const int cnt = (int)min((int64_t)tile, sd.n - n0);
-    process_tile<MODE, COV, WIN>(g, g, sd.q, n0, cnt, a, rho0, sd.idx, sd.d2, sd.cov,
-                                 smem + (size_t)warp * warp_smem_bytes(MODE), lane);
+    process_tile<MODE, COV, WIN, false, STG>(g, g, sd.q, n0, cnt, a, rho0, sd.idx, sd.d2, sd.cov,
+                                             smem + (size_t)warp * warp_bytes(MODE, STG, a.k), lane);
 }
 
 // Search over a map grown by appended points: the main grid g and the
@@ -1254,9 +1254,14 @@ cudaError_t allow_smem(K kern) {
 // The search kernel for (mode, covariance, batched) of this window variant.
 template <bool WIN>
 void* knn_kernel(int mode, bool with_cov, bool batch, bool stage = false) {
-    // outputs in host memory: the staged lane-path kernels (with covariance)
-    if (stage && !batch && with_cov && mode < 2)
-        return mode == 0 ? (void*)k_knn<0, true, WIN, true> : (void*)k_knn<1, true, WIN, true>;
+    // outputs in host memory: the staged lane-path kernels
+    if (stage && mode < 2) {
+        if (batch && with_cov)
+            return mode == 0 ? (void*)k_knn_batch<0, true, WIN, true> : (void*)k_knn_batch<1, true, WIN, true>;
+        if (batch)
+            return mode == 0 ? (void*)k_knn_batch<0, false, WIN, true> : (void*)k_knn_batch<1, false, WIN, true>;
+        if (with_cov) return mode == 0 ? (void*)k_knn<0, true, WIN, true> : (void*)k_knn<1, true, WIN, true>;
+    }
 #define PC_PICK(M, C) (batch ? (void*)k_knn_batch<M, C, WIN> : (void*)k_knn<M, C, WIN>)
     switch (mode * 2 + (with_cov ? 1 : 0)) {
         case 0: return PC_PICK(0, false);
@@ -1301,7 +1306,9 @@ cudaError_t allow_all_smem() {
             for (int b = 0; b < 2; ++b)
                 if ((e = allow_smem(knn_kernel<WIN>(mode, c != 0, b != 0))) != cudaSuccess) return e;
     for (int mode = 0; mode < 2; ++mode)
-        if ((e = allow_smem(knn_kernel<WIN>(mode, true, false, true))) != cudaSuccess) return e;
+        for (int c = 0; c < 2; ++c)
+            for (int b = 0; b < 2; ++b)
+                if ((e = allow_smem(knn_kernel<WIN>(mode, c != 0, b != 0, true))) != cudaSuccess) return e;
     return cudaSuccess;
 }
 

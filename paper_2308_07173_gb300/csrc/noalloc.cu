@@ -71,6 +71,6 @@ extern "C" pc_status pc_batch_run_noalloc(pc_target t, const pc_scan* scans, int
     e = cudaMemcpyAsync(table_dev, table, sizeof(ScanDesc) * n_scans, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess)
         e = pc_launch_knn_batch(t, t->g, t->ck, table_dev, n_scans, sh.max_n, sh.tiles, sh.tile, sh.warps, k, eps,
-                                sh.any_cov, pc_rho0(t, k), st);
+                                sh.any_cov, pc_rho0(t, k), st, sh.host_out);
     return pc_from_cuda(e);
 }

@@ -213,6 +213,23 @@ static void* mapped_host(const void* p) {
     return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
 }
 
+// The address kernels use for p: p itself for device (or managed) memory,
+// the device address of mapped page-locked host memory (and *host = true),
+// null for anything else.
+static void* device_view(const void* p, bool* host) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) return const_cast<void*>(p);
+    if (a.type == cudaMemoryTypeHost && a.devicePointer) {
+        *host = true;
+        return a.devicePointer;
+    }
+    return nullptr;
+}
+
 static void free_delta(pc_target_s* t) {
     if (t->delta) {
         pc_free_grid(t->delta);
@@ -453,22 +470,10 @@ pc_status pc_batch_plan(pc_target t, const pc_scan* scans, int n_scans, int k, f
     *out = nullptr;
     pc_status r = check_target(t);
     if (r != PC_OK) return r;
-    if (!scans || n_scans < 1 || k < 1 || k > 64 || !std::isfinite(eps)) return PC_ERR_INVALID_ARG;
-    if (t->delta) return PC_ERR_INVALID_ARG;  // appended points: pc_target_compact first
-    if ((int64_t)k > t->g.m) return PC_ERR_K_GT_M;
-    bool any_cov = false;
-    for (int i = 0; i < n_scans; ++i) {
-        const pc_scan& sc = scans[i];
-        if (sc.n < 0) return PC_ERR_INVALID_ARG;
-        if (sc.n == 0) continue;
-        if (!sc.q_dev || !sc.idx_dev || !sc.d2_dev) return PC_ERR_INVALID_ARG;
-        if (!is_device_ptr(sc.q_dev) || !is_device_ptr(sc.idx_dev) || !is_device_ptr(sc.d2_dev))
-            return PC_ERR_BAD_POINTER;
-        if (sc.cov_dev) {
-            if (!is_device_ptr(sc.cov_dev)) return PC_ERR_BAD_POINTER;
-            any_cov = true;
-        }
-    }
+    if (!scans || n_scans < 1) return PC_ERR_INVALID_ARG;
+    std::vector<ScanDesc> hs(n_scans);
+    BatchShape sh;
+    if ((r = pc_batch_table(t, scans, n_scans, k, eps, hs.data(), &sh)) != PC_OK) return r;
     DeviceGuard dg(t->device);
     pc_batch_s* b = new (std::nothrow) pc_batch_s();
     if (!b) return PC_ERR_OOM;
@@ -480,23 +485,14 @@ pc_status pc_batch_plan(pc_target t, const pc_scan* scans, int n_scans, int k, f
     b->n_scans = n_scans;
     b->k = k;
     b->eps = eps;
-    b->with_cov = any_cov;
-    b->tile = std::min(std::max(t->tune.tile, 1), 32);
-    b->warps = std::min(std::max(t->tune.warps, 1), 8);
-    std::vector<ScanDesc> hs(n_scans);
-    int64_t tiles = 0, queries = 0;
-    for (int i = 0; i < n_scans; ++i) {
-        hs[i].q = scans[i].q_dev;
-        hs[i].n = scans[i].n;
-        hs[i].idx = scans[i].idx_dev;
-        hs[i].d2 = scans[i].d2_dev;
-        hs[i].cov = scans[i].cov_dev;
-        hs[i].tile0 = tiles;
-        tiles += (scans[i].n + b->tile - 1) / b->tile;
-        queries += scans[i].n;
-        b->max_n = std::max<int64_t>(b->max_n, scans[i].n);
-    }
-    b->total_tiles = tiles;
+    b->with_cov = sh.any_cov;
+    b->host_out = sh.host_out;
+    b->tile = sh.tile;
+    b->warps = sh.warps;
+    b->max_n = sh.max_n;
+    b->total_tiles = sh.tiles;
+    int64_t queries = 0;
+    for (int i = 0; i < n_scans; ++i) queries += scans[i].n;
     b->total_queries = queries;
     cudaError_t e = pc_knn_prepare();
     if (e == cudaSuccess) e = cudaMalloc(&b->scans_dev, sizeof(ScanDesc) * n_scans);
@@ -524,7 +520,7 @@ pc_status pc_batch_run(pc_batch b, pc_stream s) {
     if (st == nullptr)  // the legacy stream cannot be captured: launch directly
         return pc_from_cuda(pc_launch_knn_batch(b->t, b->g, b->ck, b->scans_dev, b->n_scans, b->max_n,
                                                 b->total_tiles, b->tile, b->warps, b->k, b->eps, b->with_cov,
-                                                rho0, st));
+                                                rho0, st, b->host_out));
     if (!b->exec || b->captured_on != st) {
         if (b->exec) cudaGraphExecDestroy(b->exec);
         if (b->graph) cudaGraphDestroy(b->graph);
@@ -533,7 +529,7 @@ pc_status pc_batch_run(pc_batch b, pc_stream s) {
         cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
         if (e != cudaSuccess) return pc_from_cuda(e);
         cudaError_t e2 = pc_launch_knn_batch(b->t, b->g, b->ck, b->scans_dev, b->n_scans, b->max_n, b->total_tiles,
-                                             b->tile, b->warps, b->k, b->eps, b->with_cov, rho0, st);
+                                             b->tile, b->warps, b->k, b->eps, b->with_cov, rho0, st, b->host_out);
         e = cudaStreamEndCapture(st, &b->graph);
         if (e2 != cudaSuccess) e = e2;
         if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, b->graph, 0);
@@ -567,23 +563,29 @@ pc_status pc_batch_table(const pc_target_s* t, const pc_scan* scans, int n_scans
     sh.tiles = 0;
     sh.max_n = 0;
     sh.any_cov = false;
+    sh.host_out = false;
     for (int i = 0; i < n_scans; ++i) {
         const pc_scan& sc = scans[i];
         if (sc.n < 0) return PC_ERR_INVALID_ARG;
+        const void* q = sc.q_dev;
+        void *idx = sc.idx_dev, *d2 = sc.d2_dev, *cov = sc.cov_dev;
         if (sc.n > 0) {
             if (!sc.q_dev || !sc.idx_dev || !sc.d2_dev) return PC_ERR_INVALID_ARG;
-            if (!is_device_ptr(sc.q_dev) || !is_device_ptr(sc.idx_dev) || !is_device_ptr(sc.d2_dev))
-                return PC_ERR_BAD_POINTER;
+            bool host_q = false;
+            q = device_view(sc.q_dev, &host_q);
+            idx = device_view(sc.idx_dev, &sh.host_out);
+            d2 = device_view(sc.d2_dev, &sh.host_out);
+            if (!q || !idx || !d2) return PC_ERR_BAD_POINTER;
             if (sc.cov_dev) {
-                if (!is_device_ptr(sc.cov_dev)) return PC_ERR_BAD_POINTER;
+                if (!(cov = device_view(sc.cov_dev, &sh.host_out))) return PC_ERR_BAD_POINTER;
                 sh.any_cov = true;
             }
         }
-        table[i].q = sc.q_dev;
+        table[i].q = static_cast<const float*>(q);
         table[i].n = sc.n;
-        table[i].idx = sc.idx_dev;
-        table[i].d2 = sc.d2_dev;
-        table[i].cov = sc.cov_dev;
+        table[i].idx = static_cast<int32_t*>(idx);
+        table[i].d2 = static_cast<float*>(d2);
+        table[i].cov = static_cast<float*>(cov);
         table[i].tile0 = sh.tiles;
         sh.tiles += (sc.n + sh.tile - 1) / sh.tile;
         sh.max_n = std::max<int64_t>(sh.max_n, sc.n);
@@ -619,7 +621,7 @@ pc_status pc_batch_run_scratch(pc_target t, const pc_scan* scans, int n_scans, i
                                     cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess)
         e = pc_launch_knn_batch(t, t->g, t->ck, table, n_scans, sh.max_n, sh.tiles, sh.tile, sh.warps, k, eps,
-                                sh.any_cov, pc_rho0(t, k), st);
+                                sh.any_cov, pc_rho0(t, k), st, sh.host_out);
     return pc_from_cuda(e);
 }
 

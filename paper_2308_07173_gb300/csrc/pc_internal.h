@@ -75,6 +75,7 @@ struct pc_batch_s {
     int k;
     float eps;
     bool with_cov;
+    bool host_out;  // outputs in mapped host memory: the staged kernel
     int tile;
     int warps;
     int64_t total_tiles;
@@ -129,7 +130,7 @@ cudaError_t pc_launch_cov(const pc_target_s* t, const int32_t* idx, int64_t N, i
 cudaError_t pc_launch_knn_batch(const pc_target_s* t, const pcdev::Grid& g, const CovKernel& ck,
                                 const ScanDesc* scans_dev, int nscans, int64_t max_n,
                                 int64_t total_tiles, int tile, int warps, int k, float eps,
-                                bool with_cov, float rho0, cudaStream_t s);
+                                bool with_cov, float rho0, cudaStream_t s, bool stage = false);
 
 // gicp.cu
 size_t pc_gicp_work_size();
@@ -162,9 +163,11 @@ struct BatchShape {
     int64_t max_n;  // largest scan
     int tile, warps;
     bool any_cov;   // some scan asks for covariances
+    bool host_out;  // some output is mapped page-locked host memory (staged block writes)
 };
-// Argument checks and scan table shared by pc_batch_run_scratch and
-// pc_batch_run_noalloc; fills table[0, n_scans).
+// Argument checks and scan table shared by pc_batch_plan,
+// pc_batch_run_scratch and pc_batch_run_noalloc; fills table[0, n_scans)
+// with the addresses kernels use (mapped host memory translated).
 pc_status pc_batch_table(const pc_target_s* t, const pc_scan* scans, int n_scans, int k, float eps,
                          ScanDesc* table, BatchShape* shape);
 pc_status pc_from_cuda(cudaError_t e);

@@ -18,6 +18,11 @@ GPU).  The map's grid stays resident on the device.  The loop:
   slot's own stream: host-to-device copies, the batched kernel and
   device-to-host copies are queued on that stream, so a new step's copies
   and kernel overlap the steps already on the GPU;
+* or, with ``in_place=True``, points the step's scan table at the requests'
+  page-locked scans and the slot's page-locked outputs: the batched kernel
+  reads the scans and writes the results in host memory itself (each warp
+  its tile's rows as whole blocks), with no copies and no device buffers
+  beyond the scan table;
 * retires steps whose completion event has fired, frees their slot, and
   stamps each request's completion time.
 
@@ -134,13 +139,17 @@ class Server:
     the free device memory by default) sizes the slots: each slot's scan
     table and per-point buffers (12 + 8k + 24 bytes a point) share it, so a
     step holds up to capacity = (budget / slots - table) / point bytes
-    points, capped by max_step_points."""
+    points, capped by max_step_points.  With in_place the slots hold no
+    per-point device buffers (the kernel reads the requests' page-locked
+    scans and writes the slot's page-locked outputs), so the capacity is
+    max_step_points and the budget covers the scan tables alone."""
 
     def __init__(self, target: "pc.Target", k: int, eps: float, hbm_budget: Optional[int] = None,
                  max_step_scans: int = 32, slots: int = 3, keep_results: bool = False,
-                 max_step_points: int = 1 << 20):
+                 max_step_points: int = 1 << 20, in_place: bool = False):
         import torch
 
+        self.in_place = bool(in_place)
         self.t = target
         self.k = int(k)
         self.eps = float(eps)
@@ -154,22 +163,25 @@ class Server:
         self.scratch_bytes = pc.pc_batch_scratch_bytes(self.max_step)
         self.scratch = [torch.empty(self.scratch_bytes, dtype=torch.uint8, device=self.dev)
                         for _ in range(slots)]
-        self.point_bytes = 12 + 8 * self.k + 24
+        # device bytes a point of a step holds (none in place: host memory)
+        self.point_bytes = 0 if self.in_place else 12 + 8 * self.k + 24
         per_slot = self.budget // slots - _blocks(self.scratch_bytes) - 4 * ALLOC_BLOCK
-        self.capacity = int(max(1, min(int(max_step_points), per_slot // self.point_bytes)))
+        self.capacity = int(max(1, min(int(max_step_points), per_slot // max(1, self.point_bytes))))
         self.slot_buf = [self._alloc(self.capacity) for _ in range(slots)]
         self.steps_launched = 0
         self.keep = keep_results
 
     def device_bytes(self) -> int:
         """Device memory the server holds: the slots' tables and buffers."""
-        return sum(_blocks(self.scratch_bytes) + sum(_blocks(x.numel() * x.element_size()) for x in b[1])
+        return sum(_blocks(self.scratch_bytes) + sum(_blocks(x.numel() * x.element_size()) for x in (b[1] or ()))
                    for b in self.slot_buf)
 
     def _alloc(self, cap: int):
         import torch
 
         k = self.k
+        if self.in_place:
+            return (cap, None, _pinned_outputs(cap, k))
         dev = (torch.empty((cap, 3), dtype=torch.float32, device=self.dev),
                torch.empty((cap, k), dtype=torch.int32, device=self.dev),
                torch.empty((cap, k), dtype=torch.float32, device=self.dev),
@@ -188,6 +200,8 @@ class Server:
 
         s = self.streams[slot]
         npts = sum(r.n for r in reqs)
+        if self.in_place:
+            return self._launch_in_place(slot, s, reqs, npts)
         _, (dq, di, dd, dc), (hi, hd, hc) = self._slot_buffers(slot, npts)
         descs = (pc.pc_scan * len(reqs))()
         with torch.cuda.stream(s):
@@ -208,6 +222,29 @@ class Server:
                 hi[:npts].copy_(di[:npts], non_blocking=True)
                 hd[:npts].copy_(dd[:npts], non_blocking=True)
                 hc[:npts].copy_(dc[:npts], non_blocking=True)
+            done = torch.cuda.Event()
+            done.record(s)
+        self.steps_launched += 1
+        return _Step(slot, reqs, done)
+
+    def _launch_in_place(self, slot: int, s, reqs: List[Request], npts: int) -> _Step:
+        import torch
+
+        _, _, (hi, hd, hc) = self._slot_buffers(slot, npts)
+        descs = (pc.pc_scan * len(reqs))()
+        off = 0
+        for j, r in enumerate(reqs):
+            n = r.n
+            descs[j] = pc.pc_scan(r.q_host.data_ptr() if n else 0, n, hi[off].data_ptr() if n else 0,
+                                  hd[off].data_ptr() if n else 0, hc[off].data_ptr() if n else 0)
+            r.dev = (off, n)
+            off += n
+        with torch.cuda.stream(s):
+            rc = pc.pc_batch_run_scratch_array(self.t.handle, descs, len(reqs), self.k, self.eps,
+                                               self.scratch[slot].data_ptr(), self.scratch_bytes,
+                                               int(s.cuda_stream))
+            if rc != pc.PC_OK:
+                raise pc.PcError(rc, "pc_batch_run_scratch")
             done = torch.cuda.Event()
             done.record(s)
         self.steps_launched += 1

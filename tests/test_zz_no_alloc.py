@@ -110,3 +110,32 @@ def test_noalloc_batch_matches_regular_entry_twice(gpu_lib):
     torch.cuda.synchronize()
     assert marker.item() == 1.0
     t.close()
+
+
+def test_noalloc_batch_writes_page_locked_outputs(gpu_lib):
+    """Outputs in page-locked host memory: the staged kernel writes them in
+    place, equal bit for bit to the regular entry, an empty scan untouched."""
+    pc = gpu_lib
+    tr = W.oval_1500()
+    m = tr.sample_map(200_000, seed=23)
+    g = W.rng_for(24)
+    scans = [tr.raycast(*tr.random_pose(g), g)[:n] for n in (5000, 0, 1234, 31)]
+    k, eps = 16, 1e-3
+    t = pc.Target(torch.from_numpy(m).cuda())
+    try:
+        qs = [torch.from_numpy(np.ascontiguousarray(s)).cuda() for s in scans]
+        ref = [t.knn_cov(q, k, eps) for q in qs]
+        outs = [(torch.full((len(s), k), FILL, dtype=torch.int32).pin_memory(),
+                 torch.full((len(s), k), float(FILL)).pin_memory(),
+                 torch.full((len(s), 6), float(FILL)).pin_memory()) for s in scans]
+        descs = [pc.pc_scan(q.data_ptr(), q.shape[0], o[0].data_ptr(), o[1].data_ptr(), o[2].data_ptr())
+                 for q, o in zip(qs, outs)]
+        assert pc.pc_batch_run_noalloc(t.handle, descs, k, eps, 0) == pc.PC_OK
+        torch.cuda.synchronize()
+        for (ri, rd, rc), o in zip(ref, outs):
+            assert torch.equal(o[0], ri.cpu())
+            assert torch.equal(o[1].view(torch.int32), rd.cpu().view(torch.int32))
+            assert torch.equal(o[2].view(torch.int32), rc.cpu().view(torch.int32))
+        assert t.sync_status() == pc.PC_OK
+    finally:
+        t.close()
