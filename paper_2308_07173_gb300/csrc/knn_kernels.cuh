@@ -789,6 +789,12 @@ __device__ __forceinline__ float probe_radius(const Grid& g, float qx, float qy,
 // appended points (point j of dg is g.m + j): both grids' boxes of the trial
 // radius are counted and collected in the same passes, filtered by the
 // smaller of their certified taus, and list entries from dg carry DTAG.
+//
+// With STG the outputs are page-locked host memory: each lane writes its
+// idx/d2 row and covariance into the warp's staging area `stg` (laid out as
+// the output arrays), and the warp copies each array's block of the tile out
+// in 16-byte vectors, so host memory receives whole lines instead of the
+// lanes' scattered 16-byte pieces.
 template <int CAP, bool COV, bool WIN, bool DEL, bool STG>
 __device__ void lane_tile(const Grid& g, const Grid& dg, const float* __restrict__ q, int64_t n0, int cnt,
                           const TileArgs& a, float rho0, int32_t* __restrict__ idx,
