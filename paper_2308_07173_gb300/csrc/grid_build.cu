@@ -128,15 +128,18 @@ __global__ void k_dims(float mxx, float mxy, float mxz, float ox, float oy, floa
     dims[2] = cell_of(mxz, oz, inv_h) + 1;
 }
 
+// Sort key of each point: its cell key, followed (sub = 3) by its sub-bin
+// along x, so that a cell's points end up ordered by sub-bin.
 __global__ void k_keys(const float* __restrict__ xyz, int64_t M, float ox, float oy, float oz,
-                       float inv_h, int bx, int by, u64* __restrict__ keys,
+                       float inv_h, int bx, int by, int sub, u64* __restrict__ keys,
                        uint32_t* __restrict__ vals) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= M) return;
     const int cx = cell_of(xyz[3 * i], ox, inv_h);
     const int cy = cell_of(xyz[3 * i + 1], oy, inv_h);
     const int cz = cell_of(xyz[3 * i + 2], oz, inv_h);
-    keys[i] = pack_key(cx, cy, cz, bx, by);
+    const u64 key = pack_key(cx, cy, cz, bx, by);
+    keys[i] = sub ? (key << 3) | (u64)sub_bin(cell_coord(xyz[3 * i], ox, inv_h)) : key;
     vals[i] = (uint32_t)i;
 }
 
@@ -314,19 +317,19 @@ __global__ void __launch_bounds__(RS_NT) k_rs_scatter(const u64* __restrict__ ki
 }
 
 // ---------------------------------------------------------------- cells
-__global__ void k_flags(const u64* __restrict__ keys, int64_t n, uint32_t* __restrict__ flags) {
+__global__ void k_flags(const u64* __restrict__ keys, int64_t n, int sub, uint32_t* __restrict__ flags) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    flags[i] = (i == 0 || keys[i] != keys[i - 1]) ? 1u : 0u;
+    flags[i] = (i == 0 || (keys[i] >> sub) != (keys[i - 1] >> sub)) ? 1u : 0u;
 }
 
 __global__ void k_cells(const u64* __restrict__ keys, const uint32_t* __restrict__ flags,
-                        const uint32_t* __restrict__ ord, int64_t n, u64* __restrict__ cell_keys,
+                        const uint32_t* __restrict__ ord, int64_t n, int sub, u64* __restrict__ cell_keys,
                         uint32_t* __restrict__ cell_start, uint32_t U) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     if (flags[i]) {
-        cell_keys[ord[i]] = keys[i];
+        cell_keys[ord[i]] = keys[i] >> sub;
         cell_start[ord[i]] = (uint32_t)i;
     }
     if (i == 0) cell_start[U] = (uint32_t)n;
@@ -379,6 +382,30 @@ __global__ void k_dstart(const uint32_t* __restrict__ occ, const uint32_t* __res
         u = rank[w] + (uint32_t)__popc(occ[w] & ((1u << (uint32_t)(L & 31)) - 1u));
     }
     dstart[L] = cell_start[u];
+}
+
+// Sub-cell cut words (pc_device.cuh, Grid::xcut) from the sorted keys (cell
+// key << 3 | sub-bin): each run of equal sub-bins in a cell writes the
+// counts below the sub-bins it starts, the cell's last point those above
+// its own.  Cells of 255 points or more keep the zero word (no cut).
+__global__ void k_xcut(const u64* __restrict__ keys, int64_t n, int bx, int by, int dimx, int dimy,
+                       const uint32_t* __restrict__ dstart, unsigned char* __restrict__ xcut) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const u64 key = keys[i] >> 3;
+    const int sb = (int)(keys[i] & 7u);
+    const int64_t cx = (int64_t)(key & ((1ull << bx) - 1));
+    const int64_t cy = (int64_t)((key >> bx) & ((1ull << by) - 1));
+    const int64_t cz = (int64_t)(key >> (bx + by));
+    const int64_t L = cx + (int64_t)dimx * (cy + (int64_t)dimy * cz);
+    const uint32_t s = dstart[L], cnt = dstart[L + 1] - s;
+    if (cnt >= 255u) return;
+    const uint32_t r = (uint32_t)i - s;  // rank in the cell
+    const int prev = r > 0 ? (int)(keys[i - 1] & 7u) : -1;
+    for (int b = prev + 1; b <= sb; ++b)
+        if (b >= 1) xcut[8 * L + (b - 1)] = (unsigned char)r;
+    if (r + 1 == cnt)
+        for (int b = sb + 1; b <= 8; ++b) xcut[8 * L + (b - 1)] = (unsigned char)cnt;
 }
 
 __global__ void k_popc(const uint32_t* __restrict__ occ, int64_t nw, uint32_t* __restrict__ out) {
@@ -514,7 +541,7 @@ cudaError_t count_cells(const float* xyz, int64_t M, const float o[3], float h, 
 
 void pc_free_grid(pc_target_s* t) {
     void* ps[] = {t->table, t->pts, t->xyz, t->cell_keys, t->cell_start, t->status, t->stage,
-                  t->dstart};
+                  t->dstart, t->xcut};
     for (void* p : ps)
         if (p) cudaFree(p);
     t->table = nullptr;
@@ -523,6 +550,7 @@ void pc_free_grid(pc_target_s* t) {
     t->cell_start = nullptr;
     t->status = nullptr;
     t->dstart = nullptr;
+    t->xcut = nullptr;
     t->stage = nullptr;
     t->stage_bytes = 0;
 }
@@ -609,6 +637,13 @@ pc_status pc_build_grid(const float* xyz, int64_t M, const pc_build_opts& opts, 
     PC_TRY(cudaStreamSynchronize(s));
     const int bx = bits_for(dims[0]), by = bits_for(dims[1]), bz = bits_for(dims[2]);
     if (bx > 21 || by > 21 || bz > 21) return PC_ERR_INVALID_ARG;
+    // The row index (dense cell starts) is built when it costs at most eight
+    // times the points' copy, else searches visit cells through the hash;
+    // with it, the sub-cell cut (8 bytes a grid cell) when that costs at
+    // most four times the copy.
+    const int64_t ngrid = (int64_t)dims[0] * dims[1] * dims[2];
+    const bool dense = ngrid < ((int64_t)1 << 31) && (ngrid + 1) * 4 <= 8 * 16 * M;
+    const int sub = (dense && bx + by + bz + 3 <= 64 && 8 * ngrid <= 4 * 16 * M) ? 3 : 0;
 
     // 3-4. keys and sort
     u64* keys = sc.alloc<u64>(M);
@@ -616,23 +651,23 @@ pc_status pc_build_grid(const float* xyz, int64_t M, const pc_build_opts& opts, 
     uint32_t* vals = sc.alloc<uint32_t>(M);
     uint32_t* vals_alt = sc.alloc<uint32_t>(M);
     if (!keys || !keys_alt || !vals || !vals_alt) return pc_from_cuda(sc.err);
-    k_keys<<<grid_for(M, 256), 256, 0, s>>>(xyz, M, o[0], o[1], o[2], inv_h, bx, by, keys, vals);
+    k_keys<<<grid_for(M, 256), 256, 0, s>>>(xyz, M, o[0], o[1], o[2], inv_h, bx, by, sub, keys, vals);
     PC_TRY(cudaGetLastError());
-    PC_TRY(radix_sort(keys, vals, keys_alt, vals_alt, M, bx + by + bz, sc, s));
+    PC_TRY(radix_sort(keys, vals, keys_alt, vals_alt, M, bx + by + bz + sub, sc, s));
 
     // 5. occupied cells
     uint32_t* flags = sc.alloc<uint32_t>(M);
     uint32_t* ord = sc.alloc<uint32_t>(M);
     uint32_t* total_dev = sc.alloc<uint32_t>(1);
     if (!flags || !ord || !total_dev) return pc_from_cuda(sc.err);
-    k_flags<<<grid_for(M, 256), 256, 0, s>>>(keys, M, flags);
+    k_flags<<<grid_for(M, 256), 256, 0, s>>>(keys, M, sub, flags);
     PC_TRY(scan_exclusive(flags, ord, M, total_dev, sc, s));
     uint32_t U = 0;
     PC_TRY(cudaMemcpyAsync(&U, total_dev, sizeof(U), cudaMemcpyDeviceToHost, s));
     PC_TRY(cudaStreamSynchronize(s));
     PC_TRY(cudaMalloc(&t->cell_keys, sizeof(u64) * std::max<uint32_t>(U, 1)));
     PC_TRY(cudaMalloc(&t->cell_start, sizeof(uint32_t) * ((size_t)U + 1)));
-    k_cells<<<grid_for(M, 256), 256, 0, s>>>(keys, flags, ord, M, t->cell_keys, t->cell_start, U);
+    k_cells<<<grid_for(M, 256), 256, 0, s>>>(keys, flags, ord, M, sub, t->cell_keys, t->cell_start, U);
     PC_TRY(cudaGetLastError());
 
     // 6. hash table
@@ -647,12 +682,9 @@ pc_status pc_build_grid(const float* xyz, int64_t M, const pc_build_opts& opts, 
     PC_TRY(cudaGetLastError());
 
     // 6b. row index: dense cell starts over the grid, built through an
-    // occupancy bitmap and per-word ranks in scratch memory, when they cost
-    // at most eight times the points' copy (else searches visit cells
-    // through the hash)
-    const int64_t ngrid = (int64_t)dims[0] * dims[1] * dims[2];
+    // occupancy bitmap and per-word ranks in scratch memory
     int64_t dense_words = 0;
-    if (ngrid < ((int64_t)1 << 31) && (ngrid + 1) * 4 <= 8 * 16 * M) {
+    if (dense) {
         const int64_t nwords = (ngrid + 31) / 32;
         uint32_t* occ = sc.alloc<uint32_t>(nwords);
         uint32_t* rank = sc.alloc<uint32_t>(nwords);
@@ -668,6 +700,14 @@ pc_status pc_build_grid(const float* xyz, int64_t M, const pc_build_opts& opts, 
         k_dstart<<<grid_for(ngrid + 1, 256), 256, 0, s>>>(occ, rank, t->cell_start, ngrid, U, t->dstart);
         PC_TRY(cudaGetLastError());
         dense_words = ngrid + 1;
+        if (sub) {  // 6c. sub-cell cut
+            PC_TRY(cudaMalloc(&t->xcut, sizeof(uint2) * (size_t)ngrid));
+            PC_TRY(cudaMemsetAsync(t->xcut, 0, sizeof(uint2) * (size_t)ngrid, s));
+            k_xcut<<<grid_for(M, 256), 256, 0, s>>>(keys, M, bx, by, dims[0], dims[1], t->dstart,
+                                                      reinterpret_cast<unsigned char*>(t->xcut));
+            PC_TRY(cudaGetLastError());
+            dense_words += 2 * ngrid;
+        }
     }
 
     // 7. float4 copies
@@ -700,6 +740,7 @@ pc_status pc_build_grid(const float* xyz, int64_t M, const pc_build_opts& opts, 
     g.cell_keys = t->cell_keys;
     g.cell_start = t->cell_start;
     g.dstart = t->dstart;
+    g.xcut = t->xcut;
     g.status = t->status;
     g.stats = reinterpret_cast<unsigned long long*>(reinterpret_cast<char*>(t->status) + 32);
     pc_clear_window(g);

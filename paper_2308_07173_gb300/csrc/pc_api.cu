@@ -774,6 +774,7 @@ pc_status pc_target_compact(pc_target t, pc_stream s) {
     t->cell_keys = n->cell_keys;
     t->cell_start = n->cell_start;
     t->dstart = n->dstart;
+    t->xcut = n->xcut;
     t->status = n->status;
     delete n;  // its buffers now belong to t
     free_delta(t);

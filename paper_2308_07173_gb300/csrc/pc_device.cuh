@@ -46,6 +46,12 @@ struct Grid {
     // Occupied cells are ordered by L, so a run of cells along x is one
     // contiguous range of pts, read with one pair of loads.
     const uint32_t* dstart;
+    // Sub-cell cut of the row index (null when not built): points inside a
+    // cell are ordered by their eighth of the cell along x (the sub-bin, see
+    // sub_bin), and xcut[L] packs, for b = 1..8, the number of the cell's
+    // points in sub-bins below b into byte b - 1 (byte 7 = the cell's count).
+    // A cell of 255 points or more has the all-zero word: no cut.
+    const uint2* xcut;
     int* status;
     unsigned long long* stats;  // [0] queries, [1] warp-search fallbacks, [2] exhaustive scans,
                                 // [3] lane-path candidate points
@@ -67,11 +73,23 @@ __device__ __forceinline__ bool in_window(const Grid& g, float4 p) {
            p.z <= g.whiz;
 }
 
+// The cell coordinate before rounding down: fl(fl(v - o) * inv_h).  It is
+// monotone in v, so u(p) < u(v) implies p < v.
+__device__ __forceinline__ float cell_coord(float v, float o, float inv_h) {
+    return __fmul_rn(__fsub_rn(v, o), inv_h);
+}
+
 __device__ __forceinline__ int cell_of(float v, float o, float inv_h) {
-    float t = __fmul_rn(__fsub_rn(v, o), inv_h);
+    float t = cell_coord(v, o, inv_h);
     t = floorf(t);
     t = fminf(fmaxf(t, -1073741824.0f), 1073741824.0f);
     return (int)t;
+}
+
+// The eighth of its cell a cell coordinate u falls in: floor(8 (u - floor u)),
+// 0..7 (u - floor u and the product by 8 are exact).
+__device__ __forceinline__ int sub_bin(float u) {
+    return (int)floorf(__fmul_rn(__fsub_rn(u, floorf(u)), 8.0f));
 }
 
 __device__ __forceinline__ unsigned long long pack_key(int cx, int cy, int cz, int bx, int by) {
@@ -105,6 +123,27 @@ __device__ __forceinline__ uint2 row_range(const Grid& g, int cy, int cz, int x0
     const int64_t base = (int64_t)g.dimx * ((int64_t)cy + (int64_t)g.dimy * cz);
     const uint32_t s = __ldg(&g.dstart[base + x0]);
     return make_uint2(s, __ldg(&g.dstart[base + x1 + 1]) - s);
+}
+
+// Byte b - 1 of a sub-cell cut word: the cell's points in sub-bins below b.
+__device__ __forceinline__ uint32_t cut_below(uint2 w, int b) {
+    const unsigned long long v = ((unsigned long long)w.y << 32) | w.x;
+    return (uint32_t)(v >> (8 * (b - 1))) & 255u;
+}
+
+// row_range without the points of cell x0 in sub-bins below b0 and those of
+// cell x1 in sub-bins above b1 (b0 = 0 and b1 = 7 cut nothing), through the
+// sub-cell cut; the loads of both tables are independent.
+__device__ __forceinline__ uint2 row_range_cut(const Grid& g, int cy, int cz, int x0, int x1, int b0, int b1) {
+    const int64_t base = (int64_t)g.dimx * ((int64_t)cy + (int64_t)g.dimy * cz);
+    const uint32_t s = __ldg(&g.dstart[base + x0]);
+    const uint32_t e = __ldg(&g.dstart[base + x1 + 1]);
+    const uint2 w0 = __ldg(&g.xcut[base + x0]);
+    const uint2 w1 = __ldg(&g.xcut[base + x1]);
+    const uint32_t skip = b0 > 0 ? cut_below(w0, b0) : 0u;
+    const uint32_t drop = cut_below(w1, 8) - cut_below(w1, b1 + 1);
+    const uint32_t n = e - s;  // >= skip + drop by construction; clamped all the same
+    return skip + drop <= n ? make_uint2(s + skip, n - skip - drop) : make_uint2(s, n);
 }
 
 // The pinned binary32 squared distance: fmaf(dz,dz, fmaf(dy,dy, dx*dx)).

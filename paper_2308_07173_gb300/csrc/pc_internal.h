@@ -49,6 +49,7 @@ struct pc_target_s {
     unsigned long long* cell_keys;
     uint32_t* cell_start;
     uint32_t* dstart;
+    uint2* xcut;  // sub-cell cut of the row index (Grid::xcut), or null
     int* status;  // 64 bytes: status word, then 4 u64 statistics counters at +32
     // staging for pc_knn_cov_host, grown on demand
     void* stage;

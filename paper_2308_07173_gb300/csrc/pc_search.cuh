@@ -100,10 +100,18 @@ __device__ __forceinline__ uint2 row_part(const Grid& g, float qx, float qy, flo
     const float gyz2 = (gz > 0.0f ? gz * gz : 0.0f) + (gy > 0.0f ? gy * gy : 0.0f);
     if (gyz2 * (1.0f - 0x1p-20f) > tmax) return make_uint2(0u, 0u);
     const float xw = sqrtf(fmaxf(tx - gyz2, 0.0f)) + eta;
-    const int x0 = max(lx, cell_of(__fsub_rn(qx, xw), g.ox, g.inv_h));
-    const int x1 = min(hx, cell_of(__fadd_rn(qx, xw), g.ox, g.inv_h));
+    const float ul = cell_coord(__fsub_rn(qx, xw), g.ox, g.inv_h);
+    const float uh = cell_coord(__fadd_rn(qx, xw), g.ox, g.inv_h);
+    const int c0 = cell_of(__fsub_rn(qx, xw), g.ox, g.inv_h);
+    const int c1 = cell_of(__fadd_rn(qx, xw), g.ox, g.inv_h);
+    const int x0 = max(lx, c0);
+    const int x1 = min(hx, c1);
     if (x0 > x1) return make_uint2(0u, 0u);
-    return row_range(g, cy, cz, x0, x1);
+    if (!g.xcut) return row_range(g, cy, cz, x0, x1);
+    // Inside the end cells, sub-bins wholly beyond qx -+ xw: their points
+    // have u(p) < u(qx - xw) (or > u(qx + xw)), so p lies beyond the same
+    // bound that excludes the cells before x0 and after x1.
+    return row_range_cut(g, cy, cz, x0, x1, x0 == c0 ? sub_bin(ul) : 0, x1 == c1 ? sub_bin(uh) : 7);
 }
 
 // Same visit as for_box_points through the row index: every row of the box
