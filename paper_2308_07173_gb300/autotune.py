@@ -89,16 +89,17 @@ def _time_call(fn, flush, reps: int) -> float:
 
 
 DEFAULT = {"occupancy": 12.0, "rho_scale": 0.9, "warps": 4, "tile": 32, "slots": 0, "probe": 0}
-SPACE = {"occupancy": (8.0, 12.0, 16.0), "rho_scale": (0.8, 0.9, 1.0), "warps": (2, 4, 8), "tile": (16, 32),
+SPACE = {"occupancy": (8.0, 12.0, 16.0, 24.0), "rho_scale": (0.8, 0.9, 1.0), "warps": (2, 4, 8), "tile": (16, 32),
          "slots": (0, 64), "probe": (1, 2)}
 
 
 def tune(map_xyz, queries, k: int, eps: float, space: Optional[dict] = None, rounds: int = 2, reps: int = 15,
-         cache: Optional[str] = None) -> dict:
+         cache: Optional[str] = None, start: Optional[dict] = None) -> dict:
     """Coordinate descent over `space` (parameter -> values; SPACE by
-    default) on (map_xyz [M,3], queries [N,3]) CUDA float32 tensors; returns
-    the best configuration (with its time in ms and cell size) and every
-    configuration timed, and stores the best in `cache` if given."""
+    default) on (map_xyz [M,3], queries [N,3]) CUDA float32 tensors, from
+    `start` (a configuration, e.g. an earlier best; DEFAULT otherwise);
+    returns the best configuration (with its time in ms and cell size) and
+    every configuration timed, and stores the best in `cache` if given."""
     import torch
 
     space = dict(SPACE if space is None else space)
@@ -135,6 +136,7 @@ def tune(map_xyz, queries, k: int, eps: float, space: Optional[dict] = None, rou
         return ms
 
     best = dict(DEFAULT)
+    best.update({name: start[name] for name in DEFAULT if start and name in start})
     best_ms = measure(best)
     for _ in range(rounds):
         for name, values in space.items():
@@ -197,14 +199,17 @@ def tune_workloads(names, cache: Optional[str] = None, rounds: int = 2, reps: in
             raise ValueError(name)
         md = torch.from_numpy(m).cuda()
         qd = torch.from_numpy(np.ascontiguousarray(q)).cuda()
-        res = tune(md, qd, k, 1e-3, rounds=rounds, reps=reps)
+        # the descent starts from the stored best (one parameter at a time can
+        # miss a better corner reached from a different start)
+        res = tune(md, qd, k, 1e-3, rounds=rounds, reps=reps,
+                   start=lookup(cache, k, int(md.shape[0]), n_key))
         best = res["best"]
         data = load_cache(cache)
         data[_key(k, int(md.shape[0]), n_key)] = best
         with open(cache + ".tmp", "w") as f:
             json.dump(data, f, indent=1, sort_keys=True)
         os.replace(cache + ".tmp", cache)
-        out[name] = {"best": best, "default_ms": res["grid"][0]["ms"], "configs": len(res["grid"])}
+        out[name] = {"best": best, "start_ms": res["grid"][0]["ms"], "configs": len(res["grid"])}
         print(name, json.dumps(out[name]), flush=True)
         del md, qd
         torch.cuda.empty_cache()
