@@ -640,10 +640,10 @@ pc_status pc_build_grid(const float* xyz, int64_t M, const pc_build_opts& opts, 
     // The row index (dense cell starts) is built when it costs at most eight
     // times the points' copy, else searches visit cells through the hash;
     // with it, the sub-cell cut (8 bytes a grid cell) when that costs at
-    // most four times the copy.
+    // most eight times the copy.
     const int64_t ngrid = (int64_t)dims[0] * dims[1] * dims[2];
     const bool dense = ngrid < ((int64_t)1 << 31) && (ngrid + 1) * 4 <= 8 * 16 * M;
-    const int sub = (dense && bx + by + bz + 3 <= 64 && 8 * ngrid <= 4 * 16 * M) ? 3 : 0;
+    const int sub = (dense && bx + by + bz + 3 <= 64 && 8 * ngrid <= 8 * 16 * M) ? 3 : 0;
 
     // 3-4. keys and sort
     u64* keys = sc.alloc<u64>(M);
