@@ -623,8 +623,9 @@ def run_c3(args):
     _, m = W.scan_vs_map(MAP_POINTS)
     md = torch.from_numpy(m).cuda()
     r = measure_c3(md, m, reps=min(args.steps, 50))
+    ms = r.pop("ms")
     _line("query points/sec, 64-scan batch (20k-130k each) vs 2M map, kNN(k=20)+cov", r.pop("value"),
-          r.pop("unit"), r["ms"], args, {"workload": r.pop("workload"), "queries": r["queries"]},
+          r.pop("unit"), ms, args, {"workload": r.pop("workload"), "queries": r["queries"]},
           **r, gpu_launches=1)
     return 0
 
