@@ -165,6 +165,30 @@ def test_lattice_exact_ties(gpu_lib):
     t.close()
 
 
+@pytest.mark.parametrize("cell", [1.0, 0.8, 2.0])
+def test_points_and_queries_on_sub_cell_boundaries(gpu_lib, cell):
+    """The row walks skip the eighths of their end cells beyond a query's
+    chord.  A lattice of spacing cell / 8 puts points exactly on those
+    boundaries (and on the cell faces), queries sit on lattice points,
+    midpoints and chord-length offsets, and the answers must still equal
+    brute force bit for bit, ties to the lower index."""
+    s = cell / 8.0
+    g = np.stack(np.meshgrid(np.arange(40), np.arange(9), np.arange(3), indexing="ij"), -1)
+    p = (g.reshape(-1, 3) * s).astype(np.float32)
+    p = p[np.random.default_rng(7).permutation(len(p))]
+    rng = np.random.default_rng(8)
+    q = np.concatenate([p[::7], p[::11] + np.float32([s / 2, 0, 0]), p[::13] + np.float32([s / 2, s / 2, 0]),
+                        p[::17] + rng.integers(-3, 4, (len(p[::17]), 3)).astype(np.float32) * np.float32(s / 4)])
+    t = gpu_lib.Target(dev(p), cell_size=cell)
+    for k in (5, 20, 32):
+        idx, d2, cov, st = run_knn_cov(gpu_lib, t, q, k, -1.0)
+        assert st == gpu_lib.PC_OK
+        ri, rd = oracle.knn_brute(q, p, k)
+        np.testing.assert_array_equal(idx, ri)
+        np.testing.assert_array_equal(d2.view(np.uint32), rd.view(np.uint32))
+    t.close()
+
+
 def test_duplicates_tie_break_by_index(gpu_lib):
     base = np.random.default_rng(3).random((50, 3)).astype(np.float32)
     p = base[np.random.default_rng(4).integers(0, 50, 3000)]
