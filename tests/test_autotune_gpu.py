@@ -47,3 +47,17 @@ def test_tune_rejects_bad_values(gpu_lib):
         t.set_tune(probe=3)
     t.set_tune(slots=64, probe=2)
     t.close()
+
+
+def test_tune_starts_from_a_given_configuration(gpu_lib):
+    """The descent starts from `start` (the stored best when re-tuning):
+    the first configuration timed is that one, and the best is never
+    slower than it."""
+    m = torch.from_numpy(W.uniform_box(60_000, seed=5)).cuda()
+    q = torch.from_numpy(W.uniform_box(4000, seed=6)).cuda()
+    start = {"occupancy": 16.0, "rho_scale": 1.1, "warps": 2, "tile": 32, "slots": 0, "probe": 1}
+    res = autotune.tune(m, q, 12, 1e-3, space={"warps": (2, 4)}, rounds=1, reps=3, start=start)
+    first = res["grid"][0]
+    assert all(first[k] == v for k, v in start.items())
+    assert res["best"]["ms"] <= first["ms"]
+    assert res["best"]["occupancy"] == 16.0 and res["best"]["rho_scale"] == 1.1
