@@ -631,7 +631,8 @@ def run_c3(args):
 
 
 def measure_c4(duration: float, speeds, map_points: int = 5_000_000, warm_scans: int = 20,
-               repeats: int = 3, clock_ms: int = 200) -> dict:
+               repeats: int = 3, clock_ms: int = 200, step_scans: int = 16, step_points: int = 1 << 20,
+               slots: int = 3) -> dict:
     """Serving: Poisson scans from 8 vehicles x 3 LiDARs at 20 Hz (replayed
     `speed` times faster: the arrival rate scales by `speed`) against a
     resident map; continuous batching vs one host-buffer call per scan."""
@@ -649,7 +650,8 @@ def measure_c4(duration: float, speeds, map_points: int = 5_000_000, warm_scans:
     tuned = autotune.lookup(autotune.default_cache(), K_NN, map_points, 0)
     t = autotune.apply(md, tuned) if tuned else pc.Target(md)
     serve.prepare(reqs)
-    srv = serve.Server(t, K_NN, EPS, hbm_budget=2 << 30, max_step_scans=16, slots=3, in_place=True)
+    srv = serve.Server(t, K_NN, EPS, hbm_budget=2 << 30, max_step_scans=step_scans, slots=slots, in_place=True,
+                       max_step_points=step_points)
     warm = serve.requests_from_arrivals(arr[:warm_scans])
     serve.prepare(warm)
     srv.serve(warm, speed=1e6)
@@ -657,7 +659,8 @@ def measure_c4(duration: float, speeds, map_points: int = 5_000_000, warm_scans:
     out = {"workload": f"c4_24lidars_20hz_poisson_map{map_points // 1_000_000}M_k20",
            "arrival_seconds": duration, "scans": len(reqs), "points": npts,
            "offered_points_per_s_at_1x": npts / duration, "hbm_budget_bytes": 2 << 30,
-           "max_step_scans": 16, "slots": 3, "tuned": tuned or "defaults (no cached configuration)",
+           "max_step_scans": step_scans, "max_step_points": step_points, "slots": slots,
+           "tuned": tuned or "defaults (no cached configuration)",
            "io": "both forms read the page-locked scans and write page-locked results in place "
                  "(served: one batched launch per step; per-scan: pc_knn_cov_host per scan)"}
     for name, speed in speeds:
