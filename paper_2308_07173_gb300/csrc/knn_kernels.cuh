@@ -1202,8 +1202,11 @@ __global__ void __launch_bounds__(256, 2) k_knn(Grid g, const float* __restrict_
 // state the kernel keeps k_knn's registers (a persistent version spilled at
 // the 128-register cap and ran 23 % slower than one launch over the same
 // queries concatenated).
+// At most 96 registers in the lane path with up to 32 survivors, which it
+// fits without spilling (left free, the compiler takes 111); the 64-survivor
+// and warp paths keep up to 128.
 template <int MODE, bool COV, bool WIN, bool STG = false>
-__global__ void __launch_bounds__(256, 2) k_knn_batch(Grid g, const ScanDesc* __restrict__ scans,
+__global__ void __maxnreg__(MODE == 0 ? 96 : 128) k_knn_batch(Grid g, const ScanDesc* __restrict__ scans,
                                                    int nscans, int64_t total_tiles, int tile,
                                                    TileArgs a, float rho0) {
     extern __shared__ __align__(16) unsigned char smem[];
