@@ -23,7 +23,9 @@
  *    I - (1-eps) n n^T with n the unit normal (smallest eigenvalue).
  *  - "_dev" pointers are device memory (cudaMalloc / torch CUDA tensors);
  *    the caller owns them.  A host or unregistered pointer where device
- *    memory is required returns PC_ERR_BAD_POINTER.
+ *    memory is required returns PC_ERR_BAD_POINTER.  The batched entries
+ *    (pc_scan) also take page-locked host memory mapped into the device's
+ *    address space, and pc_knn_cov_host uses such buffers in place.
  *  - Every call except pc_build_target and pc_knn_cov_host is asynchronous
  *    on the given stream (a cudaStream_t cast to void*; NULL = the legacy
  *    default stream).  Argument errors are returned synchronously and
